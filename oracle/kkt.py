@@ -1,0 +1,62 @@
+"""Optimality measures for model CCM with q = 2 (oracle).
+
+Notation. For edges l = (i, j), i < j: (BX)_l = x_i - x_j; r_l = gamma * w_l;
+p(Z) = sum_l r_l ||z_l||_2. The primal is min_X 1/2||X - A||^2 + p(BX) (model
+CCM, Sec. 1). Its Lagrangian dual, for U with ||u_l|| <= r_l, is
+f_d(U) = <A, B^T U> - 1/2 ||B^T U||^2 (weak duality: f_d(U) <= f_p(X)).
+
+Readings (the paper gives only the gap of Sec. 4):
+* eta_D = ||X - A + B^T U||_F / (1 + ||A||_F)          (stationarity in X)
+* eta_P = ||BX - prox_p(BX + U)||_F / (1 + ||A||_F)     (U in the subdifferential
+  of p at BX, as a natural residual)
+* gap   = |f_p - f_d| / (1 + |f_p| + |f_d|)             (Sec. 4)
+* kkt   = max(eta_D, eta_P)
+
+Pinned by: weak duality (gap >= 0 whenever U is feasible), exact zeros at the
+closed-form n = 2 solution and at gamma = 0, and agreement of two independent
+solvers (tests/test_oracle_solvers.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+__all__ = ["incidence", "prox_group", "kkt"]
+
+
+def incidence(edges: np.ndarray, n: int) -> sp.csr_matrix:
+    """B (m x n): row l has +1 at edges[l,0] and -1 at edges[l,1]."""
+    m = edges.shape[0]
+    rows = np.repeat(np.arange(m), 2)
+    cols = edges.reshape(-1)
+    vals = np.tile(np.array([1.0, -1.0]), m)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(m, n))
+
+
+def prox_group(V: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """Row-wise prox of r_l ||.||_2: shrink each row by r_l towards 0."""
+    nv = np.sqrt(np.sum(V * V, axis=1))
+    scale = np.zeros_like(nv)
+    big = nv > r
+    scale[big] = 1.0 - r[big] / nv[big]
+    return V * scale[:, None]
+
+
+def kkt(A, edges, w, gamma, X, U):
+    """Residuals and objectives at (X, U); returns a dict."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    B = incidence(np.asarray(edges), n)
+    r = gamma * np.asarray(w, dtype=np.float64)
+    BX = B @ X
+    BtU = B.T @ U
+    nA = np.linalg.norm(A)
+    eta_d = np.linalg.norm(X - A + BtU) / (1.0 + nA)
+    eta_p = np.linalg.norm(BX - prox_group(BX + U, r)) / (1.0 + nA)
+    fp = 0.5 * np.sum((X - A) ** 2) + np.sum(r * np.sqrt(np.sum(BX * BX, axis=1)))
+    fd = np.sum(A * BtU) - 0.5 * np.sum(BtU * BtU)
+    nu = np.sqrt(np.sum(U * U, axis=1))
+    infeas = float(np.max(np.maximum(nu - r, 0.0))) if nu.size else 0.0
+    gap = abs(fp - fd) / (1.0 + abs(fp) + abs(fd))
+    return dict(eta_d=float(eta_d), eta_p=float(eta_p), kkt=float(max(eta_d, eta_p)),
+                fp=float(fp), fd=float(fd), gap=float(gap), dual_infeas=infeas)
