@@ -1,0 +1,224 @@
+// Internal declarations shared by the libccm translation units.
+//
+// Layout used by every solver kernel: node rows (A, X, gradient, CG vectors)
+// and edge rows (multipliers U, projected y, yhat) are stored with a padded
+// leading dimension ld = round_up(d, 4); padding elements are zero and stay
+// zero under every operation. A "quad" is 4 consecutive elements of a row; a
+// group of LANES threads owns one row, lane t holding quads t, t+LANES, ...
+// (CH quads per lane), so one float4 (float32 rows) or two double2 (float64
+// rows) move a quad, and consecutive lanes touch consecutive 16/32-byte
+// pieces of the row (coalesced).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ccm.h"
+
+namespace ccm {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CCM_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t _e = (call);                                             \
+    if (_e != cudaSuccess) return ::ccm::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define CCM_TRY(call)                 \
+  do {                                \
+    int _s = (call);                  \
+    if (_s != CCM_OK) return _s;      \
+  } while (0)
+
+// ---------------------------------------------------------------- context
+enum Slot : int {
+  S_AP, S_X0, S_X1, S_G, S_DX, S_R, S_P0, S_P1, S_Q, S_MINV,
+  S_U, S_UT, S_YH, S_ALPHA, S_KIND, S_EDGES, S_CSR_OFF, S_CSR_INC, S_PART, S_CTRL,
+  S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
+  S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3,
+  S_COUNT
+};
+
+struct Ctx {
+  int device = 0;
+  int num_sms = 148;
+  size_t l2_bytes = 0;
+  void* slot_ptr[S_COUNT] = {};
+  size_t slot_size[S_COUNT] = {};
+  void* host_pinned = nullptr;   // small pinned buffer for scalar read-back
+  size_t host_pinned_size = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  ccm_profile last_profile = {};
+};
+
+Ctx* ctx_of(ccm_ctx* x);
+
+// Grow-only scratch buffer for one slot (contents not preserved on growth).
+int ws_get(Ctx* c, Slot s, size_t bytes, void** out);
+int host_scalars(Ctx* c, size_t bytes, void** out);
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------- device helpers
+template <typename T> struct Vec4;
+template <> struct Vec4<double> {
+  __device__ __forceinline__ static void load(const double* p, double (&v)[4]) {
+    double2 a = *reinterpret_cast<const double2*>(p);
+    double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ static void store(double* p, const double (&v)[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+};
+template <> struct Vec4<float> {
+  __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  __device__ __forceinline__ static void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+// A row held in registers by one lane: CH quads.
+template <typename T, int CH>
+struct RowReg {
+  T v[CH][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[c][e] = T(0);
+  }
+};
+
+// Load the lane's quads of a row (elements beyond ld are treated as zero).
+template <int LANES, int CH, typename S, typename T>
+__device__ __forceinline__ void row_load(const S* row, int ld, int lane, T (&out)[CH][4]) {
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    int q = c * LANES + lane;
+    if (4 * q < ld) {
+      S tmp[4];
+      Vec4<S>::load(row + 4 * q, tmp);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[c][e] = T(tmp[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[c][e] = T(0);
+    }
+  }
+}
+
+template <int LANES, int CH, typename S, typename T>
+__device__ __forceinline__ void row_store(S* row, int ld, int lane, const T (&in)[CH][4]) {
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    int q = c * LANES + lane;
+    if (4 * q < ld) {
+      S tmp[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) tmp[e] = S(in[c][e]);
+      Vec4<S>::store(row + 4 * q, tmp);
+    }
+  }
+}
+
+// Sum over the LANES lanes of one group (fixed butterfly: deterministic).
+template <int LANES, typename T>
+__device__ __forceinline__ T group_sum(T x, unsigned mask) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, LANES);
+  return x;
+}
+
+template <int LANES>
+__device__ __forceinline__ unsigned group_mask() {
+  if (LANES >= 32) return 0xffffffffu;
+  unsigned base = (threadIdx.x & 31) / LANES * LANES;
+  return ((1u << LANES) - 1u) << base;
+}
+
+// Deterministic grid reduction of NRED doubles.
+// Every block reduces its threads' values in a fixed order and writes one
+// partial per quantity; the last block to arrive (counter) sums the partials
+// in block order and returns true with the totals in `tot` (all its threads).
+// The counter is reset by that block, so kernels can be relaunched.
+template <int NRED>
+__device__ __forceinline__ bool grid_reduce(double (&acc)[NRED], double* partials,
+                                            unsigned* counter, double (&tot)[NRED]) {
+  __shared__ double sh[32][NRED];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+      double v = lane < nwarps ? sh[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) partials[(size_t)blockIdx.x * NRED + k] = v;
+    }
+    if (lane == 0) {
+      __threadfence();
+      unsigned prev = atomicAdd(counter, 1u);
+      is_last = (prev == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  // every thread of the last block sums a strided subset, then a fixed tree
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      v += __ldcg(partials + (size_t)b * NRED + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+      double v = lane < nwarps ? sh[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[0][k] = v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) tot[k] = sh[0][k];
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// Cluster labels of X (row stride ldx) on an edge list (labels.cu).
+int labels_device(Ctx* c, const double* X, int64_t ldx, int64_t n, int d, const int2* edges,
+                  int64_t m, int32_t* labels, int32_t* n_clusters, cudaStream_t s);
+
+// Scan helpers (device-wide exclusive scan of int32 / int64).
+int scan_exclusive_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host,
+                       cudaStream_t s);
+
+}  // namespace ccm

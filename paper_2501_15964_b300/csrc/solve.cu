@@ -1,0 +1,468 @@
+// ccm_solve_path: SSNAL for model CCM (q = 2) along a gamma path, grid engine.
+//
+// The outer loop (multiplier updates), the semismooth-Newton loop, the
+// Armijo line search and the CG loop are driven from the host; every
+// reduction and every scalar recurrence of CG runs on the device (grid_reduce
+// in the last block of each kernel), and CG kernels skip themselves once the
+// device-side stop flag is set, so CG iterations are launched in chunks with
+// one host read-back per chunk.
+#include <algorithm>
+#include <cmath>
+
+#include "ccm_internal.cuh"
+#include "solve_common.cuh"
+#include "ssnal_kernels.cuh"
+
+namespace ccm {
+
+__global__ void __launch_bounds__(256)
+k_kkt_node(const double* __restrict__ X, const double* __restrict__ Ap,
+           const double* __restrict__ G, int64_t total, double* partials, Ctl* ctl) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double a = Ap[q];
+    double btu = G[q] - (X[q] - a);
+    acc[0] += a * btu;
+    acc[1] += btu * btu;
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_KKT_N], tot) && threadIdx.x == 0) {
+    ctl->kkt[2] = tot[0];
+    ctl->kkt[3] = tot[1];
+  }
+}
+
+__global__ void k_sumsq(const double* __restrict__ v, int64_t total, double* partials,
+                        Ctl* ctl) {
+  double acc[1] = {0.0};
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x)
+    acc[0] += v[q] * v[q];
+  double tot[1];
+  if (grid_reduce<1>(acc, partials, &ctl->counter[C_TRIAL], tot) && threadIdx.x == 0)
+    ctl->dots[1] = tot[0];
+}
+
+__global__ void k_pad_rows(const double* __restrict__ src, double* __restrict__ dst, int64_t rows,
+                           int d, int ld) {
+  const int64_t total = rows * ld;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = q / ld;
+    int k = (int)(q - r * ld);
+    dst[q] = (k < d) ? src[r * d + k] : 0.0;
+  }
+}
+
+__global__ void k_unpad_rows(const double* __restrict__ src, double* __restrict__ dst,
+                             int64_t rows, int d, int ld) {
+  const int64_t total = rows * d;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = q / d;
+    int k = (int)(q - r * d);
+    dst[q] = src[r * ld + k];
+  }
+}
+
+// ---------------------------------------------------------------- edge checks / CSR
+__global__ void k_validate_edges(const int2* __restrict__ edges, int64_t m, int64_t n,
+                                 const double* __restrict__ w, int* bad) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int2 ij = edges[e];
+    bool ok = ij.x >= 0 && ij.x < ij.y && (int64_t)ij.y < n;
+    if (ok && e > 0) {
+      int2 p = edges[e - 1];
+      ok = (p.x < ij.x) || (p.x == ij.x && p.y < ij.y);
+    }
+    if (ok && w) ok = w[e] >= 0.0 && isfinite(w[e]);
+    if (!ok) atomicExch(bad, 1);
+  }
+}
+
+__global__ void k_degree(const int2* __restrict__ edges, int64_t m,
+                         unsigned long long* __restrict__ deg) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int2 ij = edges[e];
+    atomicAdd(deg + ij.x, 1ull);
+    atomicAdd(deg + ij.y, 1ull);
+  }
+}
+
+__global__ void k_fill_inc(const int2* __restrict__ edges, int64_t m,
+                           const int64_t* __restrict__ off, unsigned long long* __restrict__ cur,
+                           int2* __restrict__ inc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int2 ij = edges[e];
+    unsigned long long a = atomicAdd(cur + ij.x, 1ull);
+    unsigned long long b = atomicAdd(cur + ij.y, 1ull);
+    inc[off[ij.x] + (int64_t)a] = make_int2((int)e, ij.y);
+    inc[off[ij.y] + (int64_t)b] = make_int2((int)e, ij.x);
+  }
+}
+
+// Sort each node's incidence list by edge id (insertion sort: lists are short;
+// the result, and so every reduction order, is deterministic).
+__global__ void k_sort_inc(const int64_t* __restrict__ off, int2* __restrict__ inc, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = off[i], e = off[i + 1];
+    for (int64_t s = b + 1; s < e; ++s) {
+      int2 key = inc[s];
+      int64_t t = s - 1;
+      while (t >= b && inc[t].x > key.x) {
+        inc[t + 1] = inc[t];
+        --t;
+      }
+      inc[t + 1] = key;
+    }
+  }
+}
+
+int check_edges(Ctx* c, const int2* edges, int64_t m, int64_t n, const double* w,
+                cudaStream_t s) {
+  void* pb;
+  CCM_TRY(ws_get(c, S_SCRATCH6, 64, &pb));
+  int* bad = (int*)pb;
+  CCM_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+  if (m > 0) {
+    int blocks = (int)std::min<int64_t>((m + 255) / 256, (int64_t)c->num_sms * 8);
+    k_validate_edges<<<blocks, 256, 0, s>>>(edges, m, n, w, bad);
+    CCM_CUDA(cudaGetLastError());
+  }
+  void* hp;
+  CCM_TRY(host_scalars(c, 64, &hp));
+  CCM_CUDA(cudaMemcpyAsync(hp, bad, 4, cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaStreamSynchronize(s));
+  if (*(int*)hp) {
+    set_error("edges must satisfy 0 <= i < j < n, be sorted and unique; w finite and >= 0");
+    return CCM_ERR_INVALID_ARG;
+  }
+  return CCM_OK;
+}
+
+// CSR of B^T: off[n+1] (int64), inc[2m] {edge id, other endpoint}, per-node
+// lists in increasing edge id.
+int build_csr(Ctx* c, const int2* edges, int64_t m, int64_t n, int64_t** off_out,
+              int2** inc_out, cudaStream_t s) {
+  void *p_off, *p_inc, *p_deg;
+  CCM_TRY(ws_get(c, S_CSR_OFF, (size_t)(n + 1) * 8, &p_off));
+  CCM_TRY(ws_get(c, S_CSR_INC, (size_t)std::max<int64_t>(2 * m, 1) * 8, &p_inc));
+  CCM_TRY(ws_get(c, S_BATCH1, (size_t)(n + 1) * 8, &p_deg));
+  int64_t* off = (int64_t*)p_off;
+  unsigned long long* deg = (unsigned long long*)p_deg;
+  CCM_CUDA(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 8, s));
+  int blocks_m = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, c->num_sms * 8));
+  int blocks_n = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, c->num_sms * 8));
+  if (m > 0) k_degree<<<blocks_m, 256, 0, s>>>(edges, m, deg);
+  CCM_CUDA(cudaGetLastError());
+  CCM_TRY(scan_exclusive_i64(c, (const int64_t*)deg, off, n + 1, nullptr, s));
+  CCM_CUDA(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 8, s));
+  if (m > 0) k_fill_inc<<<blocks_m, 256, 0, s>>>(edges, m, off, deg, (int2*)p_inc);
+  k_sort_inc<<<blocks_n, 256, 0, s>>>(off, (int2*)p_inc, n);
+  CCM_CUDA(cudaGetLastError());
+  *off_out = off;
+  *inc_out = (int2*)p_inc;
+  return CCM_OK;
+}
+
+// ---------------------------------------------------------------- engine
+template <int L, int CH, typename Tc>
+struct GridEngine {
+  static int run(Ctx* c, const SolveArgs& a, cudaStream_t s) {
+    const int64_t n = a.n, m = a.m;
+    const int d = a.d;
+    const int ld = (int)round_up(d, 4);
+    const int64_t nl = n * ld, ml = m * ld;
+    const int threads = 256;
+    const int gpb = threads / L;  // groups per block
+    const int maxb = c->num_sms * 4;
+    auto nb = [&](int64_t work) {
+      return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, maxb));
+    };
+    const int b_edge = (int)std::max<int64_t>(1, std::min<int64_t>((m + gpb - 1) / gpb, maxb));
+    const int b_node = (int)std::max<int64_t>(1, std::min<int64_t>((n + gpb - 1) / gpb, maxb));
+    const int b_elem = nb(nl);
+    const int b_quad = nb((nl + 3) / 4);
+
+    void* p;
+    auto get = [&](Slot sl, size_t bytes, void** out) { return ws_get(c, sl, bytes, out); };
+    CCM_TRY(get(S_AP, nl * 8, &p)); double* Ap = (double*)p;
+    CCM_TRY(get(S_X0, nl * 8, &p)); double* Xa = (double*)p;
+    CCM_TRY(get(S_X1, nl * 8, &p)); double* Xb = (double*)p;
+    CCM_TRY(get(S_G, nl * 8, &p)); double* G = (double*)p;
+    CCM_TRY(get(S_DX, nl * sizeof(Tc), &p)); Tc* Dx = (Tc*)p;
+    CCM_TRY(get(S_R, nl * sizeof(Tc), &p)); Tc* R = (Tc*)p;
+    CCM_TRY(get(S_P0, nl * sizeof(Tc), &p)); Tc* P0 = (Tc*)p;
+    CCM_TRY(get(S_P1, nl * sizeof(Tc), &p)); Tc* P1 = (Tc*)p;
+    CCM_TRY(get(S_Q, nl * sizeof(Tc), &p)); Tc* Q = (Tc*)p;
+    CCM_TRY(get(S_MINV, n * sizeof(Tc), &p)); Tc* Minv = (Tc*)p;
+    CCM_TRY(get(S_U, std::max<int64_t>(ml, 1) * 8, &p)); double* Ua = (double*)p;
+    CCM_TRY(get(S_UT, std::max<int64_t>(ml, 1) * 8, &p)); double* Ub = (double*)p;
+    CCM_TRY(get(S_YH, std::max<int64_t>(ml, 1) * sizeof(Tc), &p)); Tc* Yh = (Tc*)p;
+    CCM_TRY(get(S_ALPHA, std::max<int64_t>(m, 1) * sizeof(Tc), &p)); Tc* alpha = (Tc*)p;
+    CCM_TRY(get(S_KIND, std::max<int64_t>(m, 1), &p)); uint8_t* kind = (uint8_t*)p;
+    CCM_TRY(get(S_PART, (size_t)maxb * 4 * 8, &p)); double* part = (double*)p;
+    CCM_TRY(get(S_CTRL, sizeof(Ctl), &p)); Ctl* ctl = (Ctl*)p;
+    void* hp;
+    CCM_TRY(host_scalars(c, sizeof(Ctl) + 64, &hp));
+    Ctl* hc = (Ctl*)hp;
+    const int2* edges = (const int2*)a.edges;
+
+    int64_t* off;
+    int2* inc;
+    CCM_TRY(build_csr(c, edges, m, n, &off, &inc, s));
+    CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    k_pad_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld);
+    k_pad_rows<<<b_elem, threads, 0, s>>>(a.X0 ? a.X0 : a.A, Xa, n, d, ld);
+    if (m > 0) {
+      if (a.U0)
+        k_pad_rows<<<nb(ml), threads, 0, s>>>(a.U0, Ua, m, d, ld);
+      else
+        CCM_CUDA(cudaMemsetAsync(Ua, 0, ml * 8, s));
+    }
+    // padding of every other node/edge buffer must be zero once
+    CCM_CUDA(cudaMemsetAsync(Ub, 0, std::max<int64_t>(ml, 1) * 8, s));
+    CCM_CUDA(cudaMemsetAsync(Xb, 0, nl * 8, s));
+    CCM_CUDA(cudaMemsetAsync(Yh, 0, std::max<int64_t>(ml, 1) * sizeof(Tc), s));
+    k_sumsq<<<b_elem, threads, 0, s>>>(Ap, nl, part, ctl);
+    CCM_CUDA(cudaGetLastError());
+    auto readback = [&]() -> int {
+      CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+      CCM_CUDA(cudaStreamSynchronize(s));
+      return CCM_OK;
+    };
+    CCM_TRY(readback());
+    const double nA = std::sqrt(hc->dots[1]);
+    const double scale = 1.0 + nA;
+
+    double* X = Xa;    // current iterate
+    double* Xt = Xb;   // trial iterate
+    double* U = Ua;    // current multipliers
+    double* Ut = Ub;   // Pi(U + sigma B X) at the last evaluated point
+    double sigma = a.opt.sigma0;
+    const bool prof = a.opt.profile != 0;
+    ccm_profile profile = {};
+    std::vector<cudaEvent_t>& ev = c->ev_pool;
+    const int CHUNK = 8;
+    if (prof && ev.size() < 2 * CHUNK) {
+      while (ev.size() < 2 * CHUNK) {
+        cudaEvent_t e;
+        CCM_CUDA(cudaEventCreate(&e));
+        ev.push_back(e);
+      }
+    }
+    const double tc_floor = sizeof(Tc) == 4 ? 1e-5 : 1e-10;
+    double gamma_cur = 0.0;
+    int any_fail = 0;
+
+    // evaluate phi, grad phi, Pi(y), yhat, alpha at Xc (one edge pass + one node pass)
+    auto evaluate = [&](const double* Xc, double* phi, double* gn, double* nout) -> int {
+      k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
+                                                        Ut, Yh, alpha, kind, m, ld, part, ctl);
+      k_node_grad<L, CH, Tc><<<b_node, threads, 0, s>>>(Xc, Ap, Ut, off, inc, alpha, kind, sigma,
+                                                        d, G, Minv, n, ld, part, ctl);
+      CCM_CUDA(cudaGetLastError());
+      CCM_TRY(readback());
+      *phi = hc->eval[1] + hc->eval[0] / sigma;
+      *gn = std::sqrt(hc->eval[2]);
+      if (nout) *nout = 0;
+      return CCM_OK;
+    };
+
+    for (int t = 0; t < a.T; ++t) {
+      const double gamma = a.gammas[t];
+      gamma_cur = gamma;
+      ccm_stats st = {};
+      double last_kkt = 1.0, last_etap = -1.0;
+      bool converged = false;
+      double gn = 0, phi = 0;
+      for (int outer = 0; outer < a.opt.max_outer; ++outer) {
+        const double eps_in = std::max(0.5 * a.tol, 0.1 * last_kkt);
+        CCM_TRY(evaluate(X, &phi, &gn, nullptr));
+        for (int it = 0; it < a.opt.max_newton; ++it) {
+          if (gn / scale <= eps_in) break;
+          const double gr = gn / scale;
+          const double eta = std::min(0.1, std::max(tc_floor, std::sqrt(gr)));
+          k_cg_init<Tc><<<b_elem, threads, 0, s>>>(G, Minv, R, Dx, n, ld, eta, a.opt.max_cg,
+                                                   part, ctl);
+          CCM_CUDA(cudaGetLastError());
+          Tc* Pa = P0;
+          Tc* Pb = P1;
+          int it_before = 0;
+          for (int chunk = 0; chunk * CHUNK < a.opt.max_cg; ++chunk) {
+            for (int k = 0; k < CHUNK; ++k) {
+              if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k], s));
+              k_cg_matvec<L, CH, Tc><<<b_node, threads, 0, s>>>(
+                  Pa, Pb, R, Minv, Q, Yh, alpha, kind, off, inc, sigma, n, ld, part, ctl);
+              if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k + 1], s));
+              k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, Pb, R, Q, Minv, n, ld, part, ctl);
+              std::swap(Pa, Pb);
+            }
+            CCM_CUDA(cudaGetLastError());
+            CCM_TRY(readback());
+            if (prof) {
+              int active = hc->cg.it - it_before;
+              for (int k = 0; k < active && k < CHUNK; ++k) {
+                float ms = 0.f;
+                CCM_CUDA(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+                profile.matvec_ms_total += ms;
+                profile.matvec_launches += 1;
+                profile.matvec_bytes_total += a.matvec_bytes(hc->eval[3], k > 0 || chunk > 0,
+                                                             sizeof(Tc));
+              }
+            }
+            it_before = hc->cg.it;
+            if (!hc->cg.active) break;
+          }
+          st.cg += hc->cg.it;
+          // Armijo backtracking on phi along Dx
+          double tstep = 1.0;
+          k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
+          CCM_CUDA(cudaGetLastError());
+          CCM_TRY(readback());
+          const double gd = hc->dots[0];
+          const double slack = 1e-14 * (1.0 + std::fabs(phi));
+          double phit = 0, gnt = 0;
+          for (;;) {
+            CCM_TRY(evaluate(Xt, &phit, &gnt, nullptr));
+            st.line_search += 1;
+            if (phit <= phi + 1e-4 * tstep * gd + slack || tstep < 1e-10) break;
+            tstep *= 0.5;
+            k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
+            CCM_CUDA(cudaGetLastError());
+          }
+          std::swap(X, Xt);
+          phi = phit;
+          gn = gnt;
+          st.newton += 1;
+          if (tstep < 1e-10) break;
+        }
+        // multiplier update: U <- Pi(U + sigma B X) (computed at the last evaluation)
+        std::swap(U, Ut);
+        k_kkt_edge<L, CH><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, m, ld, part, ctl);
+        k_kkt_node<<<b_elem, threads, 0, s>>>(X, Ap, G, nl, part, ctl);
+        CCM_CUDA(cudaGetLastError());
+        CCM_TRY(readback());
+        st.outer += 1;
+        const double eta_d = gn / scale;
+        const double eta_p = std::sqrt(hc->kkt[0]) / scale;
+        const double fp = hc->eval[1] + hc->kkt[1];
+        const double fd = hc->kkt[2] - 0.5 * hc->kkt[3];
+        const double gap = std::fabs(fp - fd) / (1.0 + std::fabs(fp) + std::fabs(fd));
+        st.eta_d = eta_d;
+        st.eta_p = eta_p;
+        st.kkt = std::max(eta_d, eta_p);
+        st.f_p = fp;
+        st.f_d = fd;
+        st.gap = gap;
+        if (st.kkt <= a.tol && gap <= a.tol) {
+          converged = true;
+          break;
+        }
+        if (last_etap >= 0 && eta_p > 0.2 * last_etap) sigma = std::min(3.0 * sigma, a.opt.sigma_max);
+        last_etap = eta_p;
+        last_kkt = st.kkt;
+      }
+      st.sigma = sigma;
+      st.status = converged ? CCM_OK : CCM_ERR_NOT_CONVERGED;
+      if (!converged) any_fail = 1;
+      k_unpad_rows<<<nb(n * d), threads, 0, s>>>(X, a.Xout + (int64_t)t * n * d, n, d, ld);
+      if (a.Uout && m > 0)
+        k_unpad_rows<<<nb(m * d), threads, 0, s>>>(U, a.Uout + (int64_t)t * m * d, m, d, ld);
+      CCM_CUDA(cudaGetLastError());
+      if (a.stats) a.stats[t] = st;
+    }
+    if (prof) c->last_profile = profile;
+    return any_fail ? CCM_ERR_NOT_CONVERGED : CCM_OK;
+  }
+};
+
+// Dispatch on (lanes per row, quads per lane) from ld/4 and on precision.
+template <typename Tc>
+static int run_grid(Ctx* c, const SolveArgs& a, cudaStream_t s) {
+  const int nq = (int)(round_up(a.d, 4) / 4);
+  if (nq <= 1) return GridEngine<1, 1, Tc>::run(c, a, s);
+  if (nq <= 2) return GridEngine<2, 1, Tc>::run(c, a, s);
+  if (nq <= 4) return GridEngine<4, 1, Tc>::run(c, a, s);
+  if (nq <= 8) return GridEngine<8, 1, Tc>::run(c, a, s);
+  if (nq <= 16) return GridEngine<16, 1, Tc>::run(c, a, s);
+  if (nq <= 32) return GridEngine<32, 1, Tc>::run(c, a, s);
+  if (nq <= 64) return GridEngine<32, 2, Tc>::run(c, a, s);
+  if (nq <= 128) return GridEngine<32, 4, Tc>::run(c, a, s);
+  if (nq <= 256) return GridEngine<32, 8, Tc>::run(c, a, s);
+  set_error("d = %d exceeds the compiled maximum %d", a.d, ccm_max_dim());
+  return CCM_ERR_UNSUPPORTED;
+}
+
+int solve_grid(Ctx* c, const SolveArgs& a, cudaStream_t s) {
+  return a.opt.precision == CCM_PREC_FP64 ? run_grid<double>(c, a, s) : run_grid<float>(c, a, s);
+}
+
+}  // namespace ccm
+
+using namespace ccm;
+
+extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
+                              const int32_t* edges, const double* w, int64_t m,
+                              const double* gammas, int32_t T, int32_t q, double tol,
+                              const ccm_options* opt, double* X, int32_t* labels, double* U,
+                              ccm_stats* stats, ccm_stream_t stream) {
+  Ctx* c = ctx_of(x);
+  if (!c || !A || !X || !gammas || n < 1 || d < 1 || m < 0 || T < 1 || (m > 0 && (!edges || !w)) ||
+      !(tol > 0) || n > INT32_MAX || m > INT32_MAX) {
+    set_error("ccm_solve_path: invalid argument");
+    return CCM_ERR_INVALID_ARG;
+  }
+  if (q != 2) {
+    set_error("ccm_solve_path: only q = 2 is implemented (got q = %d)", q);
+    return CCM_ERR_UNSUPPORTED;
+  }
+  if (d > ccm_max_dim()) {
+    set_error("ccm_solve_path: d = %d exceeds the maximum %d", d, ccm_max_dim());
+    return CCM_ERR_UNSUPPORTED;
+  }
+  for (int t = 0; t < T; ++t) {
+    if (!(gammas[t] >= 0) || !std::isfinite(gammas[t]) || (t > 0 && gammas[t] < gammas[t - 1])) {
+      set_error("ccm_solve_path: gammas must be finite, >= 0 and non-decreasing");
+      return CCM_ERR_INVALID_ARG;
+    }
+  }
+  if (((uintptr_t)edges) % 8 || ((uintptr_t)A) % 8 || ((uintptr_t)X) % 8) {
+    set_error("ccm_solve_path: misaligned pointer");
+    return CCM_ERR_INVALID_ARG;
+  }
+  ccm_options o;
+  ccm_default_options(&o);
+  if (opt) o = *opt;
+  if (o.max_outer < 1 || o.max_newton < 1 || o.max_cg < 1 || !(o.sigma0 > 0) ||
+      !(o.sigma_max >= o.sigma0)) {
+    set_error("ccm_solve_path: invalid options");
+    return CCM_ERR_INVALID_ARG;
+  }
+  CCM_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  CCM_TRY(check_edges(c, (const int2*)edges, m, n, w, s));
+  SolveArgs a;
+  a.A = A; a.n = n; a.d = d; a.edges = edges; a.w = w; a.m = m;
+  a.gammas = gammas; a.T = T; a.tol = tol; a.opt = o; a.Xout = X; a.Uout = U;
+  a.stats = stats; a.X0 = o.X0; a.U0 = o.U0;
+  c->last_profile = ccm_profile{};
+  int st = solve_grid(c, a, s);
+  if (st != CCM_OK && st != CCM_ERR_NOT_CONVERGED) return st;
+  if (labels) {
+    for (int t = 0; t < T; ++t) {
+      int32_t nc = 0;
+      CCM_TRY(labels_device(c, X + (int64_t)t * n * d, d, n, d, (const int2*)edges, m,
+                            labels + (int64_t)t * n, stats ? &nc : nullptr, s));
+      if (stats) stats[t].n_clusters = nc;
+    }
+  }
+  CCM_CUDA(cudaStreamSynchronize(s));
+  if (st == CCM_ERR_NOT_CONVERGED) set_error("ccm_solve_path: some gamma hit an iteration cap");
+  return st;
+}

@@ -1,0 +1,42 @@
+// Arguments of one path solve, shared by the solver engines.
+#pragma once
+
+#include "ccm_internal.cuh"
+
+namespace ccm {
+
+struct SolveArgs {
+  const double* A = nullptr;
+  int64_t n = 0;
+  int d = 0;
+  const int32_t* edges = nullptr;
+  const double* w = nullptr;
+  int64_t m = 0;
+  const double* gammas = nullptr;  // host
+  int T = 0;
+  double tol = 1e-6;
+  ccm_options opt{};
+  double* Xout = nullptr;
+  double* Uout = nullptr;
+  ccm_stats* stats = nullptr;      // host
+  const double* X0 = nullptr;
+  const double* U0 = nullptr;
+
+  // Algorithmic bytes of one Newton-CG operator launch (each datum once):
+  // R and (after the first iteration) P_old read, P_new and Q written
+  // (n x ld each), Minv (n), yhat rows and alpha of the m_out outside edges,
+  // kind (m bytes), CSR offsets (n+1 int64) and incidences (2m int2).
+  double matvec_bytes(double m_out, bool with_pold, size_t tcb) const {
+    const double ld = (double)((d + 3) / 4 * 4);
+    const double vec = (double)n * ld * (double)tcb;
+    return vec * (with_pold ? 4.0 : 3.0) + (double)n * tcb + m_out * (ld + 1.0) * tcb +
+           (double)m + 8.0 * (double)(n + 1) + 16.0 * (double)m;
+  }
+};
+
+int solve_grid(Ctx* c, const SolveArgs& a, cudaStream_t s);
+int check_edges(Ctx* c, const int2* edges, int64_t m, int64_t n, const double* w, cudaStream_t s);
+int build_csr(Ctx* c, const int2* edges, int64_t m, int64_t n, int64_t** off_out, int2** inc_out,
+              cudaStream_t s);
+
+}  // namespace ccm

@@ -1,0 +1,438 @@
+// SSNAL building blocks for model CCM, q = 2 (Sec. 1 names the method).
+//
+// Notation (restated from convex analysis; the paper prints no formulas for
+// SSNAL): edges l = (i, j), i < j; (BX)_l = x_i - x_j; r_l = gamma w_l;
+// Pi = row-wise projection onto {||u_l|| <= r_l}; sigma = AL penalty.
+//   y_l        = u_l + sigma (x_i - x_j)
+//   phi(X)     = 1/2||X - A||^2 + (1/sigma) sum_l h_l(y_l)  (+ a constant)
+//   h_l(y)     = ||y||^2/2 if ||y|| <= r_l, else r_l||y|| - r_l^2/2
+//   grad phi   = X - A + B^T Pi(y)
+//   V          = I + sigma B^T P B,  P_l = I (||y_l|| <= r_l, r_l > 0),
+//                P_l = (r_l/||y_l||)(I - yhat_l yhat_l^T) (||y_l|| > r_l),
+//                P_l = 0 (r_l = 0)
+// The scatter B^T(.) is a deterministic pull through the CSR of B^T: node i
+// visits its incident edges in increasing edge id; the contribution of edge
+// l to node i is +(.)_l if i is its first endpoint and -(.)_l otherwise. For the
+// operator, both signs give P_l (p_i - p_other), so no sign is needed there.
+#pragma once
+
+#include "ccm_internal.cuh"
+
+namespace ccm {
+
+enum EdgeKind : uint8_t { K_INERT = 0, K_IN = 1, K_OUT = 2 };
+
+// Device-resident scalars of one solve (one problem).
+struct CgCtl {
+  double rz, rr, tol2, alpha, beta;
+  int it, maxit, active, pad;
+};
+struct Ctl {
+  CgCtl cg;
+  double eval[4];   // sum_h, 1/2||X-A||^2, ||G||^2, number of outside edges
+  double dots[2];   // <G, Dx>
+  double kkt[4];    // ||BX - prox(BX+U)||^2, sum r||BX||, <A, B^T U>, ||B^T U||^2
+  unsigned counter[8];
+};
+enum CounterId { C_EVAL_E = 0, C_EVAL_N, C_CGI, C_MV, C_UPD, C_TRIAL, C_KKT_E, C_KKT_N };
+
+struct GridShape {
+  int blocks, threads;
+};
+
+// ------------------------------------------------------------ edge evaluation
+// For every edge: y, ||y||, kind, Pi(y) -> Ut, yhat -> Yh (outside edges),
+// alpha; accumulates sum_l h_l(y_l).
+template <int LANES, int CH, typename Tc>
+__global__ void __launch_bounds__(256)
+k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
+            const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
+            double sigma, double* __restrict__ Ut, Tc* __restrict__ Yh, Tc* __restrict__ alpha,
+            uint8_t* __restrict__ kind, int64_t m, int ld, double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t e = g0; e < m; e += ng) {
+    int2 ij = edges[e];
+    double r = gamma * w[e];
+    double xi[CH][4], xj[CH][4], y[CH][4];
+    row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, xi);
+    row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, xj);
+    row_load<LANES, CH>(U + e * ld, ld, lane, y);
+    double ss = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        y[c][k] = fma(sigma, xi[c][k] - xj[c][k], y[c][k]);
+        ss = fma(y[c][k], y[c][k], ss);
+      }
+    ss = group_sum<LANES>(ss, mask);
+    double ny = sqrt(ss);
+    uint8_t kd;
+    double scale, a;
+    if (!(r > 0.0)) {
+      kd = K_INERT; scale = 0.0; a = 0.0;
+    } else if (ny <= r) {
+      kd = K_IN; scale = 1.0; a = 1.0;
+    } else {
+      kd = K_OUT; scale = r / ny; a = r / ny;
+    }
+    double h = (ny <= r) ? 0.5 * ss : r * ny - 0.5 * r * r;
+    if (lane == 0) {
+      acc[0] += h;
+      acc[1] += (kd == K_OUT) ? 1.0 : 0.0;
+      kind[e] = kd;
+      alpha[e] = (Tc)a;
+    }
+    double o[CH][4];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) o[c][k] = scale * y[c][k];
+    row_store<LANES, CH>(Ut + e * ld, ld, lane, o);
+    if (kd == K_OUT) {
+      double inv = 1.0 / ny;
+      Tc yh[CH][4];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)(y[c][k] * inv);
+      row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
+    }
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_E], tot) && threadIdx.x == 0) {
+    ctl->eval[0] = tot[0];
+    ctl->eval[3] = tot[1];
+  }
+}
+
+// ------------------------------------------------------------ node gradient
+// G_i = x_i - a_i + sum_l +-Ut_l ; also Jacobi scalars Minv_i = 1/(1 + sigma sum_l t_l)
+// with t_l = 1 (inside) or alpha_l (d-1)/d (outside) = trace(P_l)/d.
+template <int LANES, int CH, typename Tc>
+__global__ void __launch_bounds__(256)
+k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
+            const double* __restrict__ Ut, const int64_t* __restrict__ off,
+            const int2* __restrict__ inc, const Tc* __restrict__ alpha,
+            const uint8_t* __restrict__ kind, double sigma, int d, double* __restrict__ G,
+            Tc* __restrict__ Minv, int64_t n, int ld, double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % LANES;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  const double tr_out = (double)(d - 1) / (double)d;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = g0; i < n; i += ng) {
+    double g[CH][4], a[CH][4];
+    row_load<LANES, CH>(X + i * ld, ld, lane, g);
+    row_load<LANES, CH>(Ap + i * ld, ld, lane, a);
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        g[c][k] -= a[c][k];
+        acc[1] += 0.5 * g[c][k] * g[c][k];
+      }
+    double diag = 0.0;
+    const int64_t b = off[i], eend = off[i + 1];
+    for (int64_t t = b; t < eend; ++t) {
+      int2 eo = inc[t];
+      double u[CH][4];
+      row_load<LANES, CH>(Ut + (int64_t)eo.x * ld, ld, lane, u);
+      if (i < eo.y) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) g[c][k] += u[c][k];
+      } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) g[c][k] -= u[c][k];
+      }
+      uint8_t kd = kind[eo.x];
+      diag += kd == K_IN ? 1.0 : (kd == K_OUT ? (double)alpha[eo.x] * tr_out : 0.0);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[0] += g[c][k] * g[c][k];
+    row_store<LANES, CH>(G + i * ld, ld, lane, g);
+    if (lane == 0) Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_N], tot) && threadIdx.x == 0) {
+    ctl->eval[2] = tot[0];
+    ctl->eval[1] = tot[1];
+  }
+}
+
+// ------------------------------------------------------------ CG
+// R = -G, Dx = 0; rr = <R,R>, rz = <R, Minv R>; tol2 = eta^2 rr.
+template <typename Tc>
+__global__ void __launch_bounds__(256)
+k_cg_init(const double* __restrict__ G, const Tc* __restrict__ Minv, Tc* __restrict__ R,
+          Tc* __restrict__ Dx, int64_t n, int ld, double eta, int maxit, double* partials,
+          Ctl* ctl) {
+  double acc[2] = {0.0, 0.0};
+  const int64_t total = n * ld;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    Tc r = (Tc)(-G[t]);
+    R[t] = r;
+    Dx[t] = (Tc)0;
+    double rd = (double)r;
+    acc[0] += rd * rd;
+    acc[1] += rd * rd * (double)Minv[t / ld];
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_CGI], tot) && threadIdx.x == 0) {
+    CgCtl& c = ctl->cg;
+    c.rr = tot[0];
+    c.rz = tot[1];
+    c.tol2 = eta * eta * tot[0];
+    c.alpha = 0.0;
+    c.beta = 0.0;
+    c.it = 0;
+    c.maxit = maxit;
+    c.active = (tot[0] > c.tol2 && maxit > 0 && tot[1] > 0.0) ? 1 : 0;
+  }
+}
+
+// Pnew = Minv R + beta Pold; Q = V Pnew = Pnew + sigma B^T P B Pnew; pq = <Pnew, Q>.
+// Node-parallel pull over the CSR of B^T; the neighbour's Pnew row is rebuilt
+// from its R and Pold rows (those are not written by this kernel).
+template <int LANES, int CH, typename Tc>
+__global__ void __launch_bounds__(256)
+k_cg_matvec(const Tc* __restrict__ Pold, Tc* __restrict__ Pnew, const Tc* __restrict__ R,
+            const Tc* __restrict__ Minv, Tc* __restrict__ Q, const Tc* __restrict__ Yh,
+            const Tc* __restrict__ alpha, const uint8_t* __restrict__ kind,
+            const int64_t* __restrict__ off, const int2* __restrict__ inc, double sigma,
+            int64_t n, int ld, double* partials, Ctl* ctl) {
+  if (!ctl->cg.active) return;
+  const Tc beta = (Tc)ctl->cg.beta;
+  const bool use_old = ctl->cg.beta != 0.0;
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  const Tc sg = (Tc)sigma;
+  double acc[1] = {0.0};
+  for (int64_t i = g0; i < n; i += ng) {
+    Tc p[CH][4], tmp[CH][4], accv[CH][4];
+    const Tc mi = Minv[i];
+    row_load<LANES, CH>(R + i * ld, ld, lane, p);
+    if (use_old) {
+      row_load<LANES, CH>(Pold + i * ld, ld, lane, tmp);
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[c][k] = mi * p[c][k] + beta * tmp[c][k];
+    } else {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[c][k] = mi * p[c][k];
+    }
+    row_store<LANES, CH>(Pnew + i * ld, ld, lane, p);
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) accv[c][k] = (Tc)0;
+    const int64_t b = off[i], eend = off[i + 1];
+    for (int64_t t = b; t < eend; ++t) {
+      const int2 eo = inc[t];
+      const uint8_t kd = kind[eo.x];
+      if (kd == K_INERT) continue;
+      Tc v[CH][4];
+      const Tc mo = Minv[eo.y];
+      row_load<LANES, CH>(R + (int64_t)eo.y * ld, ld, lane, v);
+      if (use_old) {
+        row_load<LANES, CH>(Pold + (int64_t)eo.y * ld, ld, lane, tmp);
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[c][k] = p[c][k] - (mo * v[c][k] + beta * tmp[c][k]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[c][k] = p[c][k] - mo * v[c][k];
+      }
+      if (kd == K_OUT) {
+        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, tmp);
+        Tc s = (Tc)0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) s += tmp[c][k] * v[c][k];
+        s = group_sum<LANES>(s, mask);
+        const Tc a = alpha[eo.x];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) accv[c][k] += a * (v[c][k] - s * tmp[c][k]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) accv[c][k] += v[c][k];
+      }
+    }
+    Tc dot = (Tc)0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        accv[c][k] = p[c][k] + sg * accv[c][k];
+        dot += p[c][k] * accv[c][k];
+      }
+    acc[0] += (double)dot;
+    row_store<LANES, CH>(Q + i * ld, ld, lane, accv);
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, partials, &ctl->counter[C_MV], tot) && threadIdx.x == 0) {
+    CgCtl& c = ctl->cg;
+    if (tot[0] > 0.0 && isfinite(tot[0])) {
+      c.alpha = c.rz / tot[0];
+    } else {
+      c.alpha = 0.0;
+      c.active = 0;     // breakdown: keep the current iterate
+    }
+  }
+}
+
+// Dx += alpha P; R -= alpha Q; rz = <R, Minv R>, rr = <R,R>; beta, stop test.
+template <typename Tc>
+__global__ void __launch_bounds__(256)
+k_cg_update(Tc* __restrict__ Dx, const Tc* __restrict__ P, Tc* __restrict__ R,
+            const Tc* __restrict__ Q, const Tc* __restrict__ Minv, int64_t n, int ld,
+            double* partials, Ctl* ctl) {
+  if (!ctl->cg.active) return;
+  const Tc al = (Tc)ctl->cg.alpha;
+  double acc[2] = {0.0, 0.0};
+  const int64_t total = n * ld;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; t4 < total;
+       t4 += stride * 4) {
+    Tc dx[4], p[4], r[4], q[4];
+    Vec4<Tc>::load(Dx + t4, dx);
+    Vec4<Tc>::load(P + t4, p);
+    Vec4<Tc>::load(R + t4, r);
+    Vec4<Tc>::load(Q + t4, q);
+    const Tc mi = Minv[t4 / ld];
+    Tc rr = (Tc)0, rz = (Tc)0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      dx[k] += al * p[k];
+      r[k] -= al * q[k];
+      rr += r[k] * r[k];
+    }
+    rz = mi * rr;
+    Vec4<Tc>::store(Dx + t4, dx);
+    Vec4<Tc>::store(R + t4, r);
+    acc[0] += (double)rz;
+    acc[1] += (double)rr;
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_UPD], tot) && threadIdx.x == 0) {
+    CgCtl& c = ctl->cg;
+    c.it += 1;
+    c.beta = (c.rz > 0.0) ? tot[0] / c.rz : 0.0;
+    c.rz = tot[0];
+    c.rr = tot[1];
+    if (!(tot[1] > c.tol2) || c.it >= c.maxit || !isfinite(tot[1]) || !(tot[0] > 0.0))
+      c.active = 0;
+  }
+}
+
+// ------------------------------------------------------------ line search
+// Xt = X + t Dx; gd = <G, Dx>.
+template <typename Tc>
+__global__ void __launch_bounds__(256)
+k_trial(const double* __restrict__ X, const Tc* __restrict__ Dx, const double* __restrict__ G,
+        double t, double* __restrict__ Xt, int64_t total, double* partials, Ctl* ctl) {
+  double acc[1] = {0.0};
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double dx = (double)Dx[q];
+    Xt[q] = X[q] + t * dx;
+    acc[0] += G[q] * dx;
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc, partials, &ctl->counter[C_TRIAL], tot) && threadIdx.x == 0)
+    ctl->dots[0] = tot[0];
+}
+
+// ------------------------------------------------------------ KKT / objectives
+// Per edge: BX_l, prox residual ||BX - prox_p(BX + U)||^2 and r_l ||BX_l||.
+template <int LANES, int CH>
+__global__ void __launch_bounds__(256)
+k_kkt_edge(const double* __restrict__ X, const double* __restrict__ U,
+           const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
+           int64_t m, int ld, double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t e = g0; e < m; e += ng) {
+    int2 ij = edges[e];
+    double r = gamma * w[e];
+    double bx[CH][4], v[CH][4];
+    row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, bx);
+    row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, v);
+    double sb = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        bx[c][k] -= v[c][k];
+        sb += bx[c][k] * bx[c][k];
+      }
+    row_load<LANES, CH>(U + e * ld, ld, lane, v);
+    double sv = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[c][k] += bx[c][k];
+        sv += v[c][k] * v[c][k];
+      }
+    sb = group_sum<LANES>(sb, mask);
+    sv = group_sum<LANES>(sv, mask);
+    double nv = sqrt(sv);
+    double shrink = (nv > r) ? 1.0 - r / nv : 0.0;
+    double sres = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double res = bx[c][k] - shrink * v[c][k];
+        sres += res * res;
+      }
+    acc[0] += sres;
+    if (lane == 0) acc[1] += r * sqrt(sb);
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {
+    ctl->kkt[0] = tot[0];
+    ctl->kkt[1] = tot[1];
+  }
+}
+
+// Per node: B^T U = G - (X - A); <A, B^T U>, ||B^T U||^2.
+__global__ void __launch_bounds__(256)
+k_kkt_node(const double* __restrict__ X, const double* __restrict__ Ap,
+           const double* __restrict__ G, int64_t total, double* partials, Ctl* ctl);
+
+// ------------------------------------------------------------ layout
+__global__ void k_pad_rows(const double* __restrict__ src, double* __restrict__ dst, int64_t rows,
+                           int d, int ld);
+__global__ void k_unpad_rows(const double* __restrict__ src, double* __restrict__ dst,
+                             int64_t rows, int d, int ld);
+
+}  // namespace ccm

@@ -1,0 +1,121 @@
+"""GPU parity of ccm_solve_path against the CPU oracle (model CCM, Sec. 1;
+gap of Sec. 4).
+
+Bar: X within 1e-6 relative (Frobenius, per gamma) of the oracle solved to
+KKT <= 1e-11; KKT residuals and the relative gap recomputed by the oracle from
+the GPU's (X, U) <= 1e-6; labels bit-exact with the oracle's labelling of the
+GPU's X, and with the oracle's labels of its own X where no edge distance lies
+in the ambiguous band [1e-8, 1e-4].
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import graph as ograph
+from oracle import kkt as okkt
+from oracle import labels as olabels
+from oracle import ssnal as ossnal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ccm():
+    import paper_2501_15964_b300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _to_dev(A, edges, w):
+    dev = torch.device("cuda:0")
+    return (torch.tensor(A, device=dev), torch.tensor(edges, dtype=torch.int32, device=dev),
+            torch.tensor(w, device=dev))
+
+
+def _ambiguous(X, edges):
+    d = np.sqrt(np.sum((X[edges[:, 0]] - X[edges[:, 1]]) ** 2, axis=1))
+    return np.any((d > 1e-8) & (d < 1e-4))
+
+
+def _check_path(ccm, A, edges, w, gammas, precision, xtol=TOL):
+    Xo, _, _ = ossnal.solve_path(A, edges, w, gammas, tol=1e-11)
+    At, Et, wt = _to_dev(A, edges, w)
+    X, lab, U, stats = ccm.solve_path(At, Et, wt, gammas, tol=TOL, return_U=True,
+                                      precision=precision)
+    X = X.cpu().numpy()
+    U = U.cpu().numpy()
+    lab = lab.cpu().numpy()
+    for t, g in enumerate(gammas):
+        assert stats[t]["status"] == 0, stats[t]
+        den = max(np.linalg.norm(Xo[t]), 1e-300)
+        rel = np.linalg.norm(X[t] - Xo[t]) / den
+        assert rel <= xtol, (t, g, rel, stats[t])
+        res = okkt.kkt(A, edges, w, g, X[t], U[t])
+        assert res["kkt"] <= TOL and res["gap"] <= TOL, (t, g, res)
+        assert abs(res["kkt"] - stats[t]["kkt"]) <= 1e-8 + 1e-3 * res["kkt"], (res, stats[t])
+        assert np.array_equal(lab[t], olabels.labels(X[t], edges)), t
+        if not _ambiguous(Xo[t], edges) and not _ambiguous(X[t], edges):
+            assert np.array_equal(lab[t], olabels.labels(Xo[t], edges)), t
+        assert stats[t]["n_clusters"] == lab[t].max() + 1
+    return X, stats
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gmm200_path_matches_oracle(ccm, precision):
+    A, _, wl = synth.make_workload("gmm200_d2", 0)
+    edges, w, _ = ograph.build_graph(A, wl.k, wl.phi)
+    gammas = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    _check_path(ccm, A, edges, w, gammas, precision)
+
+
+@pytest.mark.parametrize("seed,n,d,k", [(1, 40, 1, 4), (2, 50, 3, 5), (3, 45, 7, 6),
+                                         (4, 60, 17, 5), (5, 33, 64, 4)])
+def test_small_random_paths(ccm, seed, n, d, k):
+    rng = np.random.default_rng(seed)
+    cent = rng.normal(0, 3, size=(3, d))
+    A = cent[rng.integers(0, 3, n)] + 0.8 * rng.normal(size=(n, d))
+    A[1] = A[0]                                     # a duplicate point
+    edges, w, _ = ograph.build_graph(A, k, 0.0)
+    w[::7] = 0.0                                    # inert edges
+    gammas = np.array([0.0, 0.01, 0.1, 0.5, 2.0, 50.0])
+    _check_path(ccm, A, edges, w, gammas, 1)
+
+
+def test_rejects_bad_input(ccm):
+    A, _, wl = synth.make_workload("gmm200_d2", 0, n=30)
+    edges, w, _ = ograph.build_graph(A, 4, 0.5)
+    At, Et, wt = _to_dev(A, edges, w)
+    with pytest.raises(ccm.CCMError):
+        ccm.solve_path(At, Et, wt, [0.1], q=1)
+    bad = edges.copy()
+    bad[3] = [5, 5]
+    with pytest.raises(ccm.CCMError):
+        ccm.solve_path(At, torch.tensor(bad, dtype=torch.int32, device="cuda:0"), wt, [0.1])
+    bad = edges.copy()
+    bad[0, 1] = 30                                  # out of range
+    with pytest.raises(ccm.CCMError):
+        ccm.solve_path(At, torch.tensor(bad, dtype=torch.int32, device="cuda:0"), wt, [0.1])
+    with pytest.raises(ccm.CCMError):
+        ccm.solve_path(At, Et, wt, [0.5, 0.1])      # decreasing gammas
+
+
+def test_deterministic(ccm):
+    A, _, wl = synth.make_workload("gmm200_d2", 1, n=120)
+    edges, w, _ = ograph.build_graph(A, 8, 0.5)
+    At, Et, wt = _to_dev(A, edges, w)
+    g = [0.05, 0.3, 1.5]
+    X1, L1, _, _ = ccm.solve_path(At, Et, wt, g)
+    X2, L2, _, _ = ccm.solve_path(At, Et, wt, g)
+    assert torch.equal(X1, X2) and torch.equal(L1, L2)
+
+
+def test_labels_entry_point(ccm):
+    X = np.array([[0.0, 0.0], [0.0, 1e-6], [0.0, 3e-6], [5.0, 5.0], [5.0, 5.0]])
+    E = np.array([[0, 1], [1, 2], [2, 3], [3, 4]])
+    lab, K = ccm.labels(torch.tensor(X, device="cuda:0"),
+                        torch.tensor(E, dtype=torch.int32, device="cuda:0"))
+    assert lab.cpu().tolist() == olabels.labels(X, E).tolist() == [0, 0, 1, 2, 2]
+    assert K == 3
