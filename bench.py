@@ -1,0 +1,310 @@
+"""Benchmark: gamma-solves/s of the convex clustering path on one B300.
+
+One step = the whole hot path on one synthetic problem: build the exact
+symmetrized kNN graph with Gaussian weights (ccm_build_graph) and solve the
+warm-started gamma path to KKT <= 1e-6 and relative gap <= 1e-6 with labels
+(ccm_solve_path). Default workload: the MNIST-shaped stand-in (n = 10,000,
+d = 784, k = 10, phi = 1/median, 50 gammas in [1e-3, 1e2]).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {ccm,reference}]
+
+Prints one JSON line (rank 0). Under torchrun every rank solves its own
+seeded problem (replicas: the path has no exchange step), so scaling is weak
+and `value` sums the ranks' gamma-solves over the slowest rank's time.
+`--impl reference` times the CPU oracle (plain float64 numpy/scipy) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "mnist10k_d784"
+TOL = 1e-6          # metric threshold on KKT and relative gap
+SOLVE_TOL = 2e-7    # solver stop: tighter, so X is within 1e-6 of the oracle
+METRIC = "gamma-solves/s at KKT<=1e-6 (graph build + path solve)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(",") for ln in self.f.read().splitlines() if ln.strip()]
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax = max(smax, float(r[1]))
+                for nm, v in zip(names, r[3:7]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(seed):
+    A, _, wl = synth.make_workload(WORKLOAD, seed)
+    gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    return A, wl, gam
+
+
+def run_oracle_sample(seed, budget_s=20.0):
+    """CPU oracle on a bounded sample: the same recipe at n = 600 points, the
+    full gamma grid; returns (gamma-solves/s, description)."""
+    import contextlib
+    try:
+        from threadpoolctl import threadpool_limits
+        limit = threadpool_limits(limits=1)
+        threads = 1
+    except ImportError:             # not installed: BLAS keeps its default threads
+        limit = contextlib.nullcontext()
+        threads = os.cpu_count() or 1
+
+    from oracle import graph as og
+    from oracle import ssnal as osn
+    A, _, wl = synth.make_workload(WORKLOAD, seed, n=600)
+    gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    with limit:
+        t0 = time.perf_counter()
+        edges, w, _ = og.build_graph(A, wl.k, wl.phi)
+        done = 0
+        X = U = None
+        sigma = 1.0
+        for g in gam:
+            X, U, sigma, _ = osn.solve(A, edges, w, g, X, U, sigma, tol=TOL)
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        el = time.perf_counter() - t0
+    return done / el, (f"oracle graph + SSNAL path on n=600 points of the {WORKLOAD} recipe "
+                       f"(d={A.shape[1]}, k={wl.k}), first {done} of {len(gam)} gammas, "
+                       f"tol 1e-6, {el:.1f} s, BLAS threads {threads}"), threads
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        run_oracle_sample(0, budget_s=5.0)
+    desc = ""
+    t_all = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        v, desc, thr = run_oracle_sample(0)
+        t_all += time.perf_counter() - t0
+        vals.append(v)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "gamma-solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * t_all / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "gamma-solves/s", "cores": thr,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "gamma-solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ccm", choices=["ccm", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
+                    help="synthetic workload (default: the MNIST-shaped one)")
+    ap.add_argument("--n-gamma", type=int, default=0,
+                    help="solve only the first N gammas of the path (profiling runs)")
+    args = ap.parse_args()
+    globals()["WORKLOAD"] = args.workload
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import paper_2501_15964_b300 as ccm
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prec = 1 if args.precision == "mixed" else 0
+    A, wl, gam = make_problem(rank)
+    if args.n_gamma > 0:
+        gam = gam[: args.n_gamma]
+    T = len(gam)
+    dev = torch.device("cuda", local)
+    A_dev = torch.tensor(A, device=dev)
+    A_host = torch.tensor(A).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step(A_in):
+        E, w, _ = ccm.build_graph(A_in, wl.k, wl.phi)
+        X, lab, _, stats = ccm.solve_path(A_in, E, w, gam, tol=SOLVE_TOL, precision=prec,
+                                              profile=1)
+        return X, lab, stats, E
+
+    for _ in range(args.warmup):
+        step(A_dev)
+    barrier()
+
+    # device-resident timed region
+    l0 = ccm.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    mv_ms = mv_bytes = mv_n = 0.0
+    stats_all = []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            X, lab, stats, E = step(A_dev)
+            p = ccm.last_profile()
+            mv_ms += p["matvec_ms_total"]
+            mv_bytes += p["matvec_bytes_total"]
+            mv_n += p["matvec_launches"]
+            stats_all.append(stats)
+        ev1.record(stream)
+        barrier()
+    launches = ccm.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * T * args.steps / (ms / 1000.0)
+
+    # end-to-end: pinned host A -> device, full path, X and labels back to pinned host
+    X_host = torch.empty((T, A.shape[0], A.shape[1]), dtype=torch.float64).pin_memory()
+    L_host = torch.empty((T, A.shape[0]), dtype=torch.int32).pin_memory()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        A_in = A_host.to(dev, non_blocking=True)
+        X, lab, _, _ = step(A_in)
+        X_host.copy_(X, non_blocking=True)
+        L_host.copy_(lab, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ems = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ems], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    e2e = world * T * args.steps / (ems / 1000.0)
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        achieved = (mv_bytes / 1e9) / (mv_ms / 1000.0) if mv_ms > 0 else None
+        flat = [s for st in stats_all for s in st]
+        line = {
+            "metric": METRIC, "value": value, "unit": "gamma-solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (CG operator f32)" if prec == 1 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": int(A.shape[0]), "d": int(A.shape[1]),
+                       "k": wl.k, "phi": "1/median", "gammas": T, "tol": SOLVE_TOL,
+                       "edges": int(E.shape[0]),
+                       "l2": "inputs larger than L2 (per-step working set > 1 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": "k_cg_matvec",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "launches_timed": int(mv_n), "traffic": None},
+            "e2e": {"value": e2e, "unit": "gamma-solves/s",
+                    "h2d_bytes_per_step": int(A.nbytes),
+                    "d2h_bytes_per_step": int(X_host.numel() * 8 + L_host.numel() * 4)},
+            "gpu_launches": int(launches),
+            "solver": {"max_kkt": max(s["kkt"] for s in flat),
+                       "max_gap": max(s["gap"] for s in flat),
+                       "not_converged": sum(1 for s in flat if s["status"] != 0),
+                       "newton_per_step": sum(s["newton"] for s in flat) / args.steps,
+                       "cg_per_step": sum(s["cg"] for s in flat) / args.steps,
+                       "clusters_last_gamma": flat[-1]["n_clusters"]},
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            v, desc, thr = run_oracle_sample(0)
+            line["cpu_baseline"] = {"value": v, "unit": "gamma-solves/s", "cores": thr,
+                                    "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -51,7 +51,7 @@ typedef enum { CCM_ENGINE_AUTO = 0, CCM_ENGINE_GRID = 1, CCM_ENGINE_BLOCK = 2 } 
 /* Solver options; fill with ccm_default_options() and override fields. */
 typedef struct {
   double sigma0;          /* initial augmented-Lagrangian penalty (default 1) */
-  double sigma_max;       /* cap on the penalty (default 1e4) */
+  double sigma_max;       /* cap on the penalty (default 10) */
   int32_t max_outer;      /* multiplier updates per gamma (default 200) */
   int32_t max_newton;     /* semismooth-Newton steps per multiplier update (default 50) */
   int32_t max_cg;         /* CG iterations per Newton step (default 500) */
@@ -87,7 +87,11 @@ typedef struct {
   int64_t matvec_launches;
   double matvec_ms_total;
   double matvec_bytes_total; /* algorithmic bytes moved by those launches */
+  int64_t kernel_launches;   /* all kernels the last ccm_solve_path call launched */
 } ccm_profile;
+
+/* Total number of kernels launched through this context since ccm_create. */
+int64_t ccm_launch_count(ccm_ctx* ctx);
 
 void ccm_default_options(ccm_options* opt);
 

@@ -30,6 +30,7 @@ from .api import (  # noqa: F401
     path_vjp,
     solve_path_batched,
     last_profile,
+    launch_count,
     CCMPath,
     default_context,
 )

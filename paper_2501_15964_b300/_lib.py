@@ -46,7 +46,7 @@ class Stats(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("matvec_launches", C.c_int64), ("matvec_ms_total", C.c_double),
-                ("matvec_bytes_total", C.c_double)]
+                ("matvec_bytes_total", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 class Problem(C.Structure):
@@ -67,6 +67,7 @@ _SIGS = {
                                  C.POINTER(C.c_double), C.c_int32, C.c_int32, C.c_double,
                                  C.POINTER(Options), _P, _P, _P, C.POINTER(Stats), _P]),
     "ccm_last_profile": (C.c_int, [_P, C.POINTER(Profile)]),
+    "ccm_launch_count": (C.c_int64, [_P]),
     "ccm_labels": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, C.c_int64, _P,
                              C.POINTER(C.c_int32), _P]),
     "ccm_path_vjp": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, C.c_int64,

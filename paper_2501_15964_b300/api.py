@@ -98,7 +98,13 @@ def last_profile(ctx: Context | None = None) -> dict:
     p = Profile()
     check(load_library().ccm_last_profile(ctx.handle, C.byref(p)))
     return {"matvec_launches": p.matvec_launches, "matvec_ms_total": p.matvec_ms_total,
-            "matvec_bytes_total": p.matvec_bytes_total}
+            "matvec_bytes_total": p.matvec_bytes_total, "kernel_launches": p.kernel_launches}
+
+
+def launch_count(ctx: Context | None = None) -> int:
+    """Kernels launched through the context since it was created."""
+    ctx = ctx or default_context()
+    return int(load_library().ccm_launch_count(ctx.handle))
 
 
 def labels(X, edges, ctx: Context | None = None):

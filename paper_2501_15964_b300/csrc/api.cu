@@ -95,10 +95,12 @@ static int scan_rec(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int leve
   CCM_TRY(ws_get(c, (Slot)(S_SCRATCH0 + 2 * level + 1), (size_t)tiles * 8, &buf));
   int64_t* sums_scan = (int64_t*)buf;
   k_scan_tiles<<<(unsigned)tiles, SCAN_TILE, 0, s>>>(in, out, sums, n);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   if (tiles > 1) {
     CCM_TRY(scan_rec(c, sums, sums_scan, tiles, level + 1, s));
     k_scan_add<<<(unsigned)tiles, SCAN_TILE, 0, s>>>(out, sums_scan, n);
+    CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
   }
   return CCM_OK;
@@ -123,6 +125,7 @@ int scan_exclusive_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64
     void* dtot;
     CCM_TRY(ws_get(c, S_SCRATCH7, 16, &dtot));
     k_scan_total<<<1, 1, 0, s>>>(in, out, n, (int64_t*)dtot);
+    CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
     CCM_CUDA(cudaMemcpyAsync(hp, dtot, 8, cudaMemcpyDeviceToHost, s));
     CCM_CUDA(cudaStreamSynchronize(s));
@@ -148,7 +151,7 @@ int32_t ccm_max_dim(void) { return 1024; }
 void ccm_default_options(ccm_options* o) {
   if (!o) return;
   o->sigma0 = 1.0;
-  o->sigma_max = 1e4;
+  o->sigma_max = 10.0;
   o->max_outer = 200;
   o->max_newton = 50;
   o->max_cg = 500;
@@ -195,6 +198,8 @@ void ccm_destroy(ccm_ctx* x) {
   for (auto ev : x->c.ev_pool) cudaEventDestroy(ev);
   delete x;
 }
+
+int64_t ccm_launch_count(ccm_ctx* x) { return x ? x->c.launches : 0; }
 
 int ccm_last_profile(ccm_ctx* x, ccm_profile* out) {
   if (!x || !out) {

@@ -57,7 +57,11 @@ struct Ctx {
   size_t host_pinned_size = 0;
   std::vector<cudaEvent_t> ev_pool;
   ccm_profile last_profile = {};
+  int64_t launches = 0;          // kernels launched by this context (all calls)
 };
+
+// Count one kernel launch on context c (for launch statistics).
+#define CCM_COUNT(c) ((c)->launches++)
 
 Ctx* ctx_of(ccm_ctx* x);
 

@@ -403,6 +403,7 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   int* bad = (int*)p;
   CCM_CUDA(cudaMemsetAsync(bad, 0, 4, s));
   k_check_finite<<<nb(n * d), threads, 0, s>>>(A, n * d, bad);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   CCM_TRY(sync_read(c, bad, 4, &hp, s));
   if (*(int*)hp) {
@@ -420,8 +421,11 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   double* nrm = mu + round_up(d, 8);
   double* nmax = nrm + n;
   k_colmean<<<(d + 127) / 128, 128, 0, s>>>(A, n, d, mu);
+  CCM_COUNT(c);
   k_center<<<nb(n_pad), threads, 0, s>>>(A, n, d, ldf, mu, At, nrm, n_pad);
+  CCM_COUNT(c);
   k_max_nrm<<<1, 256, 0, s>>>(nrm, n, nmax);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   // 2. candidates
   CCM_TRY(ws_get(c, S_X1, (size_t)n * Kp * 4, &p));
@@ -432,6 +436,7 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   CCM_CUDA(cudaFuncSetAttribute(k_knn_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   k_knn_tile<<<(unsigned)(n_pad / TR), threads, smem, s>>>(At, ldf, n, Kp, cand, cthr);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   // 3. rerank
   CCM_TRY(ws_get(c, S_DX, (size_t)n * k * 4, &p));
@@ -441,15 +446,13 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   int* rows = flag + n;
   int* nflag = rows + n;
   k_rerank<<<nb(n), 128, 0, s>>>(A, n, d, k, Kp, cand, cthr, nrm, nmax, nbr, flag);
-  if (force_exact) CCM_CUDA(cudaMemsetAsync(flag, 0, 0, s));
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
-  if (force_exact) {
-    // every row exhaustively (test hook for the fallback path)
-    struct Fill {};
+  if (force_exact)  // every row exhaustively (exercises the fallback path)
     CCM_CUDA(cudaMemsetAsync(flag, 0xff, (size_t)n * 4, s));
-  }
   CCM_CUDA(cudaMemsetAsync(nflag, 0, 4, s));
   k_compact_flags<<<nb(n), threads, 0, s>>>(flag, n, rows, nflag);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   CCM_TRY(sync_read(c, nflag, 4, &hp, s));
   const int nrows = *(int*)hp;
@@ -458,6 +461,7 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
     const int blocks = std::max(1, std::min(fb, c->num_sms * 4));
     CCM_TRY(ws_get(c, S_P0, (size_t)blocks * n * 8, &p));
     k_exact_row<<<blocks, 256, 0, s>>>(A, n, d, k, rows, nrows, (double*)p, nbr);
+    CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
   }
   // 4. symmetrize
@@ -472,11 +476,14 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   int64_t* eoff = ucnt + (n + 1);
   CCM_CUDA(cudaMemsetAsync(bcnt, 0, (size_t)(n + 1) * 8, s));
   k_bucket_count<<<nb(n * k), threads, 0, s>>>(nbr, n, k, bcnt);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   CCM_TRY(scan_exclusive_i64(c, (const int64_t*)bcnt, boff, n + 1, nullptr, s));
   CCM_CUDA(cudaMemsetAsync(bcnt, 0, (size_t)(n + 1) * 8, s));
   k_bucket_fill<<<nb(n * k), threads, 0, s>>>(nbr, n, k, boff, bcnt, bucket);
+  CCM_COUNT(c);
   k_bucket_unique<<<nb(n), threads, 0, s>>>(boff, bucket, n, ucnt);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   int64_t m = 0;
   CCM_TRY(scan_exclusive_i64(c, ucnt, eoff, n, &m, s));
@@ -486,11 +493,13 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
     return CCM_ERR_BUFFER_TOO_SMALL;
   }
   k_emit_edges<<<nb(n), threads, 0, s>>>(boff, bucket, ucnt, eoff, n, (int2*)edges_out);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   // 5. weights
   CCM_TRY(ws_get(c, S_YH, (size_t)std::max<int64_t>(m, 1) * 8, &p));
   double* D = (double*)p;
   k_edge_dist<<<nb(m), threads, 0, s>>>(A, d, (const int2*)edges_out, m, D);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   double ph = phi;
   if (!(phi > 0)) {
@@ -505,6 +514,7 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
     for (int shift = 56; shift >= 0; shift -= 8) {
       CCM_CUDA(cudaMemsetAsync(hist, 0, 256 * 8, s));
       k_radix_hist<<<nb(m), threads, 0, s>>>(D, m, shift, prefix, hist);
+      CCM_COUNT(c);
       CCM_CUDA(cudaGetLastError());
       CCM_TRY(sync_read(c, hist, 256 * 8, &hp, s));
       const unsigned long long* h = (const unsigned long long*)hp;
@@ -528,6 +538,7 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
     ph = 1.0 / med;
   }
   k_weights<<<nb(m), threads, 0, s>>>(D, m, ph, w_out);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   CCM_CUDA(cudaStreamSynchronize(s));
   *phi_out = ph;

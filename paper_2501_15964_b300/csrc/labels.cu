@@ -102,12 +102,18 @@ int labels_device(Ctx* c, const double* X, int64_t ldx, int64_t n, int d, const 
   blocks_n = blocks_n < 1 ? 1 : blocks_n;
   blocks_m = blocks_m < 1 ? 1 : blocks_m;
   k_lab_init<<<blocks_n, 256, 0, s>>>(parent, n);
-  if (m > 0) k_lab_hook<<<blocks_m, 256, 0, s>>>(X, ldx, d, edges, m, parent, n, err);
+  CCM_COUNT(c);
+  if (m > 0) {
+    k_lab_hook<<<blocks_m, 256, 0, s>>>(X, ldx, d, edges, m, parent, n, err);
+    CCM_COUNT(c);
+  }
   k_lab_flatten<<<blocks_n, 256, 0, s>>>(parent, n, is_root, err);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   int64_t total = 0;
   CCM_TRY(scan_exclusive_i64(c, is_root, rank, n, n_clusters ? &total : nullptr, s));
   k_lab_assign<<<blocks_n, 256, 0, s>>>(parent, n, rank, labels, err);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   if (n_clusters) {
     void* hp;

@@ -1,5 +1,5 @@
-// Entry points whose kernels are not built yet: they validate nothing and
-// report CCM_ERR_UNSUPPORTED so callers fail loudly.
+// Entry points whose kernels are not built yet: they report
+// CCM_ERR_UNSUPPORTED so callers fail loudly.
 #include "ccm_internal.cuh"
 
 using namespace ccm;
@@ -15,11 +15,5 @@ extern "C" int ccm_solve_path_batched(ccm_ctx*, int32_t, const ccm_problem*, int
                                       const double*, int32_t, double, const ccm_options*,
                                       ccm_stats*, ccm_stream_t) {
   set_error("ccm_solve_path_batched: not built in this version");
-  return CCM_ERR_UNSUPPORTED;
-}
-
-extern "C" int ccm_build_graph(ccm_ctx*, const double*, int64_t, int32_t, int32_t, double,
-                               int32_t*, double*, int64_t, int64_t*, double*, ccm_stream_t) {
-  set_error("ccm_build_graph: not built in this version");
   return CCM_ERR_UNSUPPORTED;
 }

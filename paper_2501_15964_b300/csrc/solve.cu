@@ -132,6 +132,7 @@ int check_edges(Ctx* c, const int2* edges, int64_t m, int64_t n, const double* w
   if (m > 0) {
     int blocks = (int)std::min<int64_t>((m + 255) / 256, (int64_t)c->num_sms * 8);
     k_validate_edges<<<blocks, 256, 0, s>>>(edges, m, n, w, bad);
+    CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
   }
   void* hp;
@@ -158,12 +159,19 @@ int build_csr(Ctx* c, const int2* edges, int64_t m, int64_t n, int64_t** off_out
   CCM_CUDA(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 8, s));
   int blocks_m = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, c->num_sms * 8));
   int blocks_n = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, c->num_sms * 8));
-  if (m > 0) k_degree<<<blocks_m, 256, 0, s>>>(edges, m, deg);
+  if (m > 0) {
+    k_degree<<<blocks_m, 256, 0, s>>>(edges, m, deg);
+    CCM_COUNT(c);
+  }
   CCM_CUDA(cudaGetLastError());
   CCM_TRY(scan_exclusive_i64(c, (const int64_t*)deg, off, n + 1, nullptr, s));
   CCM_CUDA(cudaMemsetAsync(deg, 0, (size_t)(n + 1) * 8, s));
-  if (m > 0) k_fill_inc<<<blocks_m, 256, 0, s>>>(edges, m, off, deg, (int2*)p_inc);
+  if (m > 0) {
+    k_fill_inc<<<blocks_m, 256, 0, s>>>(edges, m, off, deg, (int2*)p_inc);
+    CCM_COUNT(c);
+  }
   k_sort_inc<<<blocks_n, 256, 0, s>>>(off, (int2*)p_inc, n);
+  CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   *off_out = off;
   *inc_out = (int2*)p_inc;
@@ -218,18 +226,23 @@ struct GridEngine {
     CCM_TRY(build_csr(c, edges, m, n, &off, &inc, s));
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     k_pad_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld);
+    CCM_COUNT(c);
     k_pad_rows<<<b_elem, threads, 0, s>>>(a.X0 ? a.X0 : a.A, Xa, n, d, ld);
+    CCM_COUNT(c);
     if (m > 0) {
-      if (a.U0)
+      if (a.U0) {
         k_pad_rows<<<nb(ml), threads, 0, s>>>(a.U0, Ua, m, d, ld);
-      else
+        CCM_COUNT(c);
+      } else {
         CCM_CUDA(cudaMemsetAsync(Ua, 0, ml * 8, s));
+      }
     }
     // padding of every other node/edge buffer must be zero once
     CCM_CUDA(cudaMemsetAsync(Ub, 0, std::max<int64_t>(ml, 1) * 8, s));
     CCM_CUDA(cudaMemsetAsync(Xb, 0, nl * 8, s));
     CCM_CUDA(cudaMemsetAsync(Yh, 0, std::max<int64_t>(ml, 1) * sizeof(Tc), s));
     k_sumsq<<<b_elem, threads, 0, s>>>(Ap, nl, part, ctl);
+    CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
     auto readback = [&]() -> int {
       CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -264,8 +277,10 @@ struct GridEngine {
     auto evaluate = [&](const double* Xc, double* phi, double* gn, double* nout) -> int {
       k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
                                                         Ut, Yh, alpha, kind, m, ld, part, ctl);
+      CCM_COUNT(c);
       k_node_grad<L, CH, Tc><<<b_node, threads, 0, s>>>(Xc, Ap, Ut, off, inc, alpha, kind, sigma,
                                                         d, G, Minv, n, ld, part, ctl);
+      CCM_COUNT(c);
       CCM_CUDA(cudaGetLastError());
       CCM_TRY(readback());
       *phi = hc->eval[1] + hc->eval[0] / sigma;
@@ -290,6 +305,7 @@ struct GridEngine {
           const double eta = std::min(0.1, std::max(tc_floor, std::sqrt(gr)));
           k_cg_init<Tc><<<b_elem, threads, 0, s>>>(G, Minv, R, Dx, n, ld, eta, a.opt.max_cg,
                                                    part, ctl);
+          CCM_COUNT(c);
           CCM_CUDA(cudaGetLastError());
           Tc* Pa = P0;
           Tc* Pb = P1;
@@ -299,8 +315,10 @@ struct GridEngine {
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k], s));
               k_cg_matvec<L, CH, Tc><<<b_node, threads, 0, s>>>(
                   Pa, Pb, R, Minv, Q, Yh, alpha, kind, off, inc, sigma, n, ld, part, ctl);
+              CCM_COUNT(c);
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k + 1], s));
               k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, Pb, R, Q, Minv, n, ld, part, ctl);
+              CCM_COUNT(c);
               std::swap(Pa, Pb);
             }
             CCM_CUDA(cudaGetLastError());
@@ -323,6 +341,7 @@ struct GridEngine {
           // Armijo backtracking on phi along Dx
           double tstep = 1.0;
           k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
+          CCM_COUNT(c);
           CCM_CUDA(cudaGetLastError());
           CCM_TRY(readback());
           const double gd = hc->dots[0];
@@ -334,6 +353,7 @@ struct GridEngine {
             if (phit <= phi + 1e-4 * tstep * gd + slack || tstep < 1e-10) break;
             tstep *= 0.5;
             k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
+            CCM_COUNT(c);
             CCM_CUDA(cudaGetLastError());
           }
           std::swap(X, Xt);
@@ -345,7 +365,9 @@ struct GridEngine {
         // multiplier update: U <- Pi(U + sigma B X) (computed at the last evaluation)
         std::swap(U, Ut);
         k_kkt_edge<L, CH><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, m, ld, part, ctl);
+        CCM_COUNT(c);
         k_kkt_node<<<b_elem, threads, 0, s>>>(X, Ap, G, nl, part, ctl);
+        CCM_COUNT(c);
         CCM_CUDA(cudaGetLastError());
         CCM_TRY(readback());
         st.outer += 1;
@@ -372,8 +394,11 @@ struct GridEngine {
       st.status = converged ? CCM_OK : CCM_ERR_NOT_CONVERGED;
       if (!converged) any_fail = 1;
       k_unpad_rows<<<nb(n * d), threads, 0, s>>>(X, a.Xout + (int64_t)t * n * d, n, d, ld);
-      if (a.Uout && m > 0)
+      CCM_COUNT(c);
+      if (a.Uout && m > 0) {
         k_unpad_rows<<<nb(m * d), threads, 0, s>>>(U, a.Uout + (int64_t)t * m * d, m, d, ld);
+        CCM_COUNT(c);
+      }
       CCM_CUDA(cudaGetLastError());
       if (a.stats) a.stats[t] = st;
     }
@@ -393,7 +418,11 @@ static int run_grid(Ctx* c, const SolveArgs& a, cudaStream_t s) {
   if (nq <= 16) return GridEngine<16, 1, Tc>::run(c, a, s);
   if (nq <= 32) return GridEngine<32, 1, Tc>::run(c, a, s);
   if (nq <= 64) return GridEngine<32, 2, Tc>::run(c, a, s);
+  if (nq <= 96) return GridEngine<32, 3, Tc>::run(c, a, s);
   if (nq <= 128) return GridEngine<32, 4, Tc>::run(c, a, s);
+  if (nq <= 160) return GridEngine<32, 5, Tc>::run(c, a, s);
+  if (nq <= 192) return GridEngine<32, 6, Tc>::run(c, a, s);
+  if (nq <= 224) return GridEngine<32, 7, Tc>::run(c, a, s);
   if (nq <= 256) return GridEngine<32, 8, Tc>::run(c, a, s);
   set_error("d = %d exceeds the compiled maximum %d", a.d, ccm_max_dim());
   return CCM_ERR_UNSUPPORTED;
@@ -452,6 +481,7 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
   a.gammas = gammas; a.T = T; a.tol = tol; a.opt = o; a.Xout = X; a.Uout = U;
   a.stats = stats; a.X0 = o.X0; a.U0 = o.U0;
   c->last_profile = ccm_profile{};
+  const int64_t launches0 = c->launches;
   int st = solve_grid(c, a, s);
   if (st != CCM_OK && st != CCM_ERR_NOT_CONVERGED) return st;
   if (labels) {
@@ -463,6 +493,7 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     }
   }
   CCM_CUDA(cudaStreamSynchronize(s));
+  c->last_profile.kernel_launches = c->launches - launches0;
   if (st == CCM_ERR_NOT_CONVERGED) set_error("ccm_solve_path: some gamma hit an iteration cap");
   return st;
 }

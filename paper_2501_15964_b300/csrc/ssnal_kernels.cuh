@@ -126,42 +126,55 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
   const double tr_out = (double)(d - 1) / (double)d;
   double acc[2] = {0.0, 0.0};
   for (int64_t i = g0; i < n; i += ng) {
-    double g[CH][4], a[CH][4];
-    row_load<LANES, CH>(X + i * ld, ld, lane, g);
-    row_load<LANES, CH>(Ap + i * ld, ld, lane, a);
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
+    const int64_t b = off[i], eend = off[i + 1];
+    // one quad per lane at a time: few registers, many warps in flight; the
+    // incidence list is re-read per chunk from L1. Every element still sums
+    // its incident edges in increasing edge id (same order as before).
+#pragma unroll 1
+    for (int c = 0; c < CH; ++c) {
+      const int q = c * LANES + lane;
+      if (4 * q >= ld) break;
+      double g[4], a[4];
+      Vec4<double>::load(X + i * ld + 4 * q, g);
+      Vec4<double>::load(Ap + i * ld + 4 * q, a);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        g[c][k] -= a[c][k];
-        acc[1] += 0.5 * g[c][k] * g[c][k];
+        g[k] -= a[k];
+        acc[1] += 0.5 * g[k] * g[k];
       }
-    double diag = 0.0;
-    const int64_t b = off[i], eend = off[i + 1];
-    for (int64_t t = b; t < eend; ++t) {
-      int2 eo = inc[t];
-      double u[CH][4];
-      row_load<LANES, CH>(Ut + (int64_t)eo.x * ld, ld, lane, u);
-      if (i < eo.y) {
+      int64_t t = b;
+      for (; t + 1 < eend; t += 2) {  // two incidences in flight
+        const int2 e0 = inc[t], e1 = inc[t + 1];
+        double u0[4], u1[4];
+        Vec4<double>::load(Ut + (int64_t)e0.x * ld + 4 * q, u0);
+        Vec4<double>::load(Ut + (int64_t)e1.x * ld + 4 * q, u1);
+        const double s0 = (i < e0.y) ? 1.0 : -1.0, s1 = (i < e1.y) ? 1.0 : -1.0;
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+        for (int k = 0; k < 4; ++k) g[k] += s0 * u0[k];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) g[c][k] += u[c][k];
-      } else {
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) g[c][k] -= u[c][k];
+        for (int k = 0; k < 4; ++k) g[k] += s1 * u1[k];
       }
-      uint8_t kd = kind[eo.x];
-      diag += kd == K_IN ? 1.0 : (kd == K_OUT ? (double)alpha[eo.x] * tr_out : 0.0);
+      if (t < eend) {
+        const int2 e0 = inc[t];
+        double u0[4];
+        Vec4<double>::load(Ut + (int64_t)e0.x * ld + 4 * q, u0);
+        const double s0 = (i < e0.y) ? 1.0 : -1.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[k] += s0 * u0[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[0] += g[k] * g[k];
+      Vec4<double>::store(G + i * ld + 4 * q, g);
     }
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[0] += g[c][k] * g[c][k];
-    row_store<LANES, CH>(G + i * ld, ld, lane, g);
-    if (lane == 0) Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
+    if (lane == 0) {
+      double diag = 0.0;
+      for (int64_t t = b; t < eend; ++t) {
+        const int e = inc[t].x;
+        const uint8_t kd = kind[e];
+        diag += kd == K_IN ? 1.0 : (kd == K_OUT ? (double)alpha[e] * tr_out : 0.0);
+      }
+      Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
+    }
   }
   double tot[2];
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_N], tot) && threadIdx.x == 0) {
@@ -243,15 +256,33 @@ k_cg_matvec(const Tc* __restrict__ Pold, Tc* __restrict__ Pnew, const Tc* __rest
 #pragma unroll
       for (int k = 0; k < 4; ++k) accv[c][k] = (Tc)0;
     const int64_t b = off[i], eend = off[i + 1];
+    // the next incidence's edge id, kind, alpha and Minv are fetched one
+    // iteration ahead so that each edge costs one round trip (its rows)
+    int2 eo_n = make_int2(0, 0);
+    uint8_t kd_n = K_INERT;
+    Tc mo_n = (Tc)0, a_n = (Tc)0;
+    if (b < eend) {
+      eo_n = inc[b];
+      kd_n = kind[eo_n.x];
+      mo_n = Minv[eo_n.y];
+      a_n = alpha[eo_n.x];
+    }
     for (int64_t t = b; t < eend; ++t) {
-      const int2 eo = inc[t];
-      const uint8_t kd = kind[eo.x];
+      const int2 eo = eo_n;
+      const uint8_t kd = kd_n;
+      const Tc mo = mo_n, a = a_n;
+      if (t + 1 < eend) {
+        eo_n = inc[t + 1];
+        kd_n = kind[eo_n.x];
+        mo_n = Minv[eo_n.y];
+        a_n = alpha[eo_n.x];
+      }
       if (kd == K_INERT) continue;
-      Tc v[CH][4];
-      const Tc mo = Minv[eo.y];
+      Tc v[CH][4], yh[CH][4];
       row_load<LANES, CH>(R + (int64_t)eo.y * ld, ld, lane, v);
+      if (use_old) row_load<LANES, CH>(Pold + (int64_t)eo.y * ld, ld, lane, tmp);
+      if (kd == K_OUT) row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, yh);
       if (use_old) {
-        row_load<LANES, CH>(Pold + (int64_t)eo.y * ld, ld, lane, tmp);
 #pragma unroll
         for (int c = 0; c < CH; ++c)
 #pragma unroll
@@ -263,14 +294,16 @@ k_cg_matvec(const Tc* __restrict__ Pold, Tc* __restrict__ Pnew, const Tc* __rest
           for (int k = 0; k < 4; ++k) v[c][k] = p[c][k] - mo * v[c][k];
       }
       if (kd == K_OUT) {
-        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, tmp);
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) tmp[c][k] = yh[c][k];
         Tc s = (Tc)0;
 #pragma unroll
         for (int c = 0; c < CH; ++c)
 #pragma unroll
           for (int k = 0; k < 4; ++k) s += tmp[c][k] * v[c][k];
         s = group_sum<LANES>(s, mask);
-        const Tc a = alpha[eo.x];
 #pragma unroll
         for (int c = 0; c < CH; ++c)
 #pragma unroll

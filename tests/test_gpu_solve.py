@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-6
+SOLVE_TOL = 2e-7
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +44,9 @@ def _ambiguous(X, edges):
 def _check_path(ccm, A, edges, w, gammas, precision, xtol=TOL):
     Xo, _, _ = ossnal.solve_path(A, edges, w, gammas, tol=1e-11)
     At, Et, wt = _to_dev(A, edges, w)
-    X, lab, U, stats = ccm.solve_path(At, Et, wt, gammas, tol=TOL, return_U=True,
+    # the solver stops at KKT <= 2e-7 (tighter than the 1e-6 bar) so that X is also
+    # within 1e-6 of the oracle: KKT <= 1e-6 alone left 2e-6 on one gamma
+    X, lab, U, stats = ccm.solve_path(At, Et, wt, gammas, tol=SOLVE_TOL, return_U=True,
                                       precision=precision)
     X = X.cpu().numpy()
     U = U.cpu().numpy()
