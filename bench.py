@@ -101,7 +101,7 @@ def make_problem(seed):
     return A, wl, gam
 
 
-def run_oracle_sample(seed, budget_s=20.0):
+def run_oracle_sample(seed, budget_s=15.0):
     """CPU oracle on a bounded sample: the same recipe at n = 600 points, the
     full gamma grid; returns (gamma-solves/s, description)."""
     import contextlib
@@ -115,7 +115,8 @@ def run_oracle_sample(seed, budget_s=20.0):
 
     from oracle import graph as og
     from oracle import ssnal as osn
-    A, _, wl = synth.make_workload(WORKLOAD, seed, n=600)
+    n_s = 300
+    A, _, wl = synth.make_workload(WORKLOAD, seed, n=n_s)
     gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
     with limit:
         t0 = time.perf_counter()
@@ -124,12 +125,15 @@ def run_oracle_sample(seed, budget_s=20.0):
         X = U = None
         sigma = 1.0
         for g in gam:
-            X, U, sigma, _ = osn.solve(A, edges, w, g, X, U, sigma, tol=TOL)
+            # same penalty cap as the library's default; iteration caps keep one
+            # gamma bounded, the wall budget bounds the whole sample
+            X, U, sigma, _ = osn.solve(A, edges, w, g, X, U, sigma, tol=TOL, sigma_max=10.0,
+                                       max_outer=100, max_newton=30)
             done += 1
             if time.perf_counter() - t0 > budget_s:
                 break
         el = time.perf_counter() - t0
-    return done / el, (f"oracle graph + SSNAL path on n=600 points of the {WORKLOAD} recipe "
+    return done / el, (f"oracle graph + SSNAL path on n={n_s} points of the {WORKLOAD} recipe "
                        f"(d={A.shape[1]}, k={wl.k}), first {done} of {len(gam)} gammas, "
                        f"tol 1e-6, {el:.1f} s, BLAS threads {threads}"), threads
 
@@ -161,6 +165,88 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def _time(fn, stream, reps=1):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def form_batched(args):
+    """Batched form: 256 independent problems (n ~ U{500..5000}, d = 16) in one
+    persistent launch, against a loop of plain ccm_solve_path calls (grid
+    engine) on the same GPU, same tolerance."""
+    import torch
+    import paper_2501_15964_b300 as ccm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probs = synth.batched_problems(0, count=args.batch)
+    gam = probs[0]["gammas"]
+    dev = []
+    for p in probs:
+        A = torch.tensor(p["A"], device="cuda")
+        E, w, _ = ccm.build_graph(A, p["k"], p["phi"])
+        dev.append(dict(A=A, edges=E, w=w))
+    T = len(gam)
+    for _ in range(max(1, args.warmup)):
+        ccm.solve_path_batched(dev, gam, tol=SOLVE_TOL)
+    ms_b, (Xs, Ls, st) = _time(lambda: ccm.solve_path_batched(dev, gam, tol=SOLVE_TOL), stream,
+                               args.steps)
+    flat = [s for ps in st for s in ps]
+    nloop = min(args.loop, len(dev))
+
+    def loop():
+        for p in dev[:nloop]:
+            ccm.solve_path(p["A"], p["edges"], p["w"], gam, tol=SOLVE_TOL, engine=1)
+    loop()
+    ms_l, _ = _time(loop, stream, 1)
+    ms_sub, _ = _time(lambda: ccm.solve_path_batched(dev[:nloop], gam, tol=SOLVE_TOL), stream, 1)
+    line = {"form": "batched", "metric": "gamma-solves/s, batched vs loop of plain solves",
+            "unit": "gamma-solves/s", "problems": len(dev), "gammas": T, "tol": SOLVE_TOL,
+            "batched_value": len(dev) * T / (ms_b / 1000), "batched_ms": ms_b,
+            "loop_problems": nloop, "loop_value": nloop * T / (ms_l / 1000), "loop_ms": ms_l,
+            "batched_same_subset_value": nloop * T / (ms_sub / 1000),
+            "speedup_same_subset": ms_l / ms_sub,
+            "max_kkt": max(s["kkt"] for s in flat), "max_gap": max(s["gap"] for s in flat),
+            "not_converged": sum(1 for s in flat if s["status"] != 0)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def form_vjp(args):
+    """Adjoint form: dL/dA and dL/dw of sum_t ||X*(gamma_t) - T||^2 on the
+    n = 20,000, d = 64 workload, against two plain path solves (the cost of
+    one central-difference direction)."""
+    import torch
+    import paper_2501_15964_b300 as ccm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    A, _, wl = synth.make_workload("gmm20k_d64", 0)
+    gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    T = torch.tensor(synth.adjoint_target(0, A.shape[0], A.shape[1]), device="cuda")
+    At = torch.tensor(A, device="cuda")
+    E, w, _ = ccm.build_graph(At, wl.k, wl.phi)
+    X, _, _, st = ccm.solve_path(At, E, w, gam, tol=SOLVE_TOL)
+    G = 2.0 * (X - T)
+    ccm.path_vjp(At, E, w, gam, X, G)
+    ms_s, _ = _time(lambda: ccm.solve_path(At, E, w, gam, tol=SOLVE_TOL), stream, args.steps)
+    ms_v, _ = _time(lambda: ccm.path_vjp(At, E, w, gam, X, G), stream, args.steps)
+    line = {"form": "adjoint", "metric": "VJP time vs two plain path solves", "unit": "ms",
+            "workload": "gmm20k_d64", "n": int(A.shape[0]), "d": int(A.shape[1]),
+            "edges": int(E.shape[0]), "gammas": len(gam), "path_solve_ms": ms_s,
+            "vjp_ms": ms_v, "two_solves_over_vjp": 2 * ms_s / ms_v,
+            "clusters": [s["n_clusters"] for s in st]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,8 +259,17 @@ def main():
                     help="synthetic workload (default: the MNIST-shaped one)")
     ap.add_argument("--n-gamma", type=int, default=0,
                     help="solve only the first N gammas of the path (profiling runs)")
+    ap.add_argument("--form", default="path", choices=["path", "batched", "adjoint"],
+                    help="path (default, the JSON contract line), batched or adjoint comparison")
+    ap.add_argument("--batch", type=int, default=256, help="problems in the batched form")
+    ap.add_argument("--loop", type=int, default=32,
+                    help="problems solved one by one for the batched comparison")
     args = ap.parse_args()
     globals()["WORKLOAD"] = args.workload
+    if args.form == "batched":
+        return form_batched(args)
+    if args.form == "adjoint":
+        return form_vjp(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -32,9 +32,9 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
     if (_e != cudaSuccess) return ::ccm::cuda_fail(_e, #call, __FILE__, __LINE__); \
   } while (0)
 
-#define CCM_TRY(call)                 \
+#define CCM_TRY(...)                  \
   do {                                \
-    int _s = (call);                  \
+    int _s = (__VA_ARGS__);           \
     if (_s != CCM_OK) return _s;      \
   } while (0)
 

@@ -214,7 +214,8 @@ struct GridEngine {
     CCM_TRY(get(S_YH, std::max<int64_t>(ml, 1) * sizeof(Tc), &p)); Tc* Yh = (Tc*)p;
     CCM_TRY(get(S_ALPHA, std::max<int64_t>(m, 1) * sizeof(Tc), &p)); Tc* alpha = (Tc*)p;
     CCM_TRY(get(S_KIND, std::max<int64_t>(m, 1), &p)); uint8_t* kind = (uint8_t*)p;
-    CCM_TRY(get(S_PART, (size_t)maxb * 4 * 8, &p)); double* part = (double*)p;
+    CCM_TRY(get(S_PART, (size_t)kMaxPartBlocksPerSm * c->num_sms * 4 * 8, &p));
+    double* part = (double*)p;
     CCM_TRY(get(S_CTRL, sizeof(Ctl), &p)); Ctl* ctl = (Ctl*)p;
     void* hp;
     CCM_TRY(host_scalars(c, sizeof(Ctl) + 64, &hp));
@@ -313,9 +314,8 @@ struct GridEngine {
           for (int chunk = 0; chunk * CHUNK < a.opt.max_cg; ++chunk) {
             for (int k = 0; k < CHUNK; ++k) {
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k], s));
-              k_cg_matvec<L, CH, Tc><<<b_node, threads, 0, s>>>(
-                  Pa, Pb, R, Minv, Q, Yh, alpha, kind, off, inc, sigma, n, ld, part, ctl);
-              CCM_COUNT(c);
+              CCM_TRY(launch_matvec<L, CH, Tc>(c, Pa, Pb, R, Minv, nullptr, Q, Yh, alpha, kind,
+                                                off, inc, sigma, n, ld, part, ctl, s));
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k + 1], s));
               k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, Pb, R, Q, Minv, n, ld, part, ctl);
               CCM_COUNT(c);
@@ -482,6 +482,21 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
   a.stats = stats; a.X0 = o.X0; a.U0 = o.U0;
   c->last_profile = ccm_profile{};
   const int64_t launches0 = c->launches;
+  // small problems: one thread block runs the whole path (no host round trips);
+  // otherwise the grid engine spreads every phase over the whole GPU
+  const int64_t ldd = round_up(d, 4);
+  const bool small = n * ldd <= 16384 && m * ldd <= 131072 && d <= 128;
+  const bool use_block = o.engine == CCM_ENGINE_BLOCK || (o.engine == CCM_ENGINE_AUTO && small);
+  if (o.engine == CCM_ENGINE_BLOCK && d > 128) {
+    set_error("ccm_solve_path: the block engine supports d <= 128");
+    return CCM_ERR_UNSUPPORTED;
+  }
+  if (use_block) {
+    int st = solve_single_block(c, a, labels, s);
+    c->last_profile.kernel_launches = c->launches - launches0;
+    if (st == CCM_ERR_NOT_CONVERGED) set_error("ccm_solve_path: some gamma hit an iteration cap");
+    return st;
+  }
   int st = solve_grid(c, a, s);
   if (st != CCM_OK && st != CCM_ERR_NOT_CONVERGED) return st;
   if (labels) {

@@ -35,6 +35,7 @@ struct SolveArgs {
 };
 
 int solve_grid(Ctx* c, const SolveArgs& a, cudaStream_t s);
+int solve_single_block(Ctx* c, const SolveArgs& a, int32_t* labels, cudaStream_t s);
 int check_edges(Ctx* c, const int2* edges, int64_t m, int64_t n, const double* w, cudaStream_t s);
 int build_csr(Ctx* c, const int2* edges, int64_t m, int64_t n, int64_t** off_out, int2** inc_out,
               cudaStream_t s);

@@ -1,0 +1,99 @@
+"""GPU parity of the block engine and ccm_solve_path_batched against the CPU
+oracle (model CCM, Sec. 1; gap of Sec. 4): many independent problems of
+uneven size in one persistent launch."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import graph as ograph
+from oracle import kkt as okkt
+from oracle import labels as olabels
+from oracle import ssnal as ossnal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL, SOLVE_TOL = 1e-6, 2e-7
+
+
+@pytest.fixture(scope="module")
+def ccm():
+    import paper_2501_15964_b300 as m
+    return m
+
+
+def _problems(count, seed, n_lo=40, n_hi=160, d=16):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        K = int(rng.integers(2, 6))
+        k = int(rng.integers(3, 8))
+        A, _ = synth.gaussian_mixture(rng, n, d, K, 5.0, 0.5, 1.5, "equal", "normal")
+        E, w, _ = ograph.build_graph(A, k, 0.0)
+        out.append((A, E, w))
+    return out
+
+
+def _dev(A, E, w):
+    return dict(A=torch.tensor(A, device="cuda:0"),
+                edges=torch.tensor(E, dtype=torch.int32, device="cuda:0"),
+                w=torch.tensor(w, device="cuda:0"))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_matches_oracle(ccm, precision):
+    probs = _problems(12, 7)
+    gammas = synth.gamma_grid(1e-3, 1e2, 8)
+    Xs, Ls, stats = ccm.solve_path_batched([_dev(*p) for p in probs], gammas, tol=SOLVE_TOL,
+                                          precision=precision)
+    for (A, E, w), X, L, st in zip(probs, Xs, Ls, stats):
+        Xo, _, _ = ossnal.solve_path(A, E, w, gammas, tol=1e-11)
+        X = X.cpu().numpy()
+        L = L.cpu().numpy()
+        for t, g in enumerate(gammas):
+            assert st[t]["status"] == 0, st[t]
+            assert st[t]["kkt"] <= TOL and st[t]["gap"] <= TOL
+            rel = np.linalg.norm(X[t] - Xo[t]) / np.linalg.norm(Xo[t])
+            assert rel <= TOL, (t, rel)
+            assert np.array_equal(L[t], olabels.labels(X[t], E))
+            assert st[t]["n_clusters"] == L[t].max() + 1
+
+
+def test_block_engine_single_problem_kkt(ccm):
+    """ccm_solve_path with the block engine: KKT and gap recomputed by the oracle
+    from the GPU's (X, U)."""
+    A, _, wl = synth.make_workload("gmm200_d2", 2)
+    E, w, _ = ograph.build_graph(A, wl.k, wl.phi)
+    g = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    P = _dev(A, E, w)
+    X, L, U, st = ccm.solve_path(P["A"], P["edges"], P["w"], g, tol=SOLVE_TOL, return_U=True,
+                                 engine=2)
+    X = X.cpu().numpy()
+    U = U.cpu().numpy()
+    for t in range(len(g)):
+        res = okkt.kkt(A, E, w, g[t], X[t], U[t])
+        assert res["kkt"] <= TOL and res["gap"] <= TOL, res
+        assert np.array_equal(L[t].cpu().numpy(), olabels.labels(X[t], E))
+
+
+def test_batched_equals_single_block_runs(ccm):
+    """A batch gives the same X (bitwise) as solving each problem alone with the
+    block engine: the work queue changes only where a problem runs."""
+    probs = _problems(5, 11, 30, 90, d=8)
+    g = [0.01, 0.3, 3.0]
+    Xs, Ls, _ = ccm.solve_path_batched([_dev(*p) for p in probs], g, tol=SOLVE_TOL)
+    for (A, E, w), Xb, Lb in zip(probs, Xs, Ls):
+        P = _dev(A, E, w)
+        X1, L1, _, _ = ccm.solve_path(P["A"], P["edges"], P["w"], g, tol=SOLVE_TOL, engine=2)
+        assert torch.equal(Xb, X1) and torch.equal(Lb, L1)
+
+
+def test_batched_rejects_bad_problem(ccm):
+    probs = _problems(2, 3, 30, 40, d=4)
+    bad = _dev(*probs[1])
+    E = bad["edges"].clone()
+    E[0, 1] = 10 ** 6
+    bad["edges"] = E
+    with pytest.raises(ccm.CCMError):
+        ccm.solve_path_batched([_dev(*probs[0]), bad], [0.1])

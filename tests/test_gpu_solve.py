@@ -41,13 +41,13 @@ def _ambiguous(X, edges):
     return np.any((d > 1e-8) & (d < 1e-4))
 
 
-def _check_path(ccm, A, edges, w, gammas, precision, xtol=TOL):
+def _check_path(ccm, A, edges, w, gammas, precision, xtol=TOL, engine=0):
     Xo, _, _ = ossnal.solve_path(A, edges, w, gammas, tol=1e-11)
     At, Et, wt = _to_dev(A, edges, w)
     # the solver stops at KKT <= 2e-7 (tighter than the 1e-6 bar) so that X is also
     # within 1e-6 of the oracle: KKT <= 1e-6 alone left 2e-6 on one gamma
     X, lab, U, stats = ccm.solve_path(At, Et, wt, gammas, tol=SOLVE_TOL, return_U=True,
-                                      precision=precision)
+                                      precision=precision, engine=engine)
     X = X.cpu().numpy()
     U = U.cpu().numpy()
     lab = lab.cpu().numpy()
@@ -66,17 +66,19 @@ def _check_path(ccm, A, edges, w, gammas, precision, xtol=TOL):
     return X, stats
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_gmm200_path_matches_oracle(ccm, precision):
+@pytest.mark.parametrize("precision,engine", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_gmm200_path_matches_oracle(ccm, precision, engine):
+    """The n = 200, d = 2 workload on both engines (GRID = 1, BLOCK = 2)."""
     A, _, wl = synth.make_workload("gmm200_d2", 0)
     edges, w, _ = ograph.build_graph(A, wl.k, wl.phi)
     gammas = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
-    _check_path(ccm, A, edges, w, gammas, precision)
+    _check_path(ccm, A, edges, w, gammas, precision, engine=engine)
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("seed,n,d,k", [(1, 40, 1, 4), (2, 50, 3, 5), (3, 45, 7, 6),
                                          (4, 60, 17, 5), (5, 33, 64, 4)])
-def test_small_random_paths(ccm, seed, n, d, k):
+def test_small_random_paths(ccm, seed, n, d, k, engine):
     rng = np.random.default_rng(seed)
     cent = rng.normal(0, 3, size=(3, d))
     A = cent[rng.integers(0, 3, n)] + 0.8 * rng.normal(size=(n, d))
@@ -84,7 +86,7 @@ def test_small_random_paths(ccm, seed, n, d, k):
     edges, w, _ = ograph.build_graph(A, k, 0.0)
     w[::7] = 0.0                                    # inert edges
     gammas = np.array([0.0, 0.01, 0.1, 0.5, 2.0, 50.0])
-    _check_path(ccm, A, edges, w, gammas, 1)
+    _check_path(ccm, A, edges, w, gammas, 1, engine=engine)
 
 
 def test_rejects_bad_input(ccm):
@@ -110,9 +112,10 @@ def test_deterministic(ccm):
     edges, w, _ = ograph.build_graph(A, 8, 0.5)
     At, Et, wt = _to_dev(A, edges, w)
     g = [0.05, 0.3, 1.5]
-    X1, L1, _, _ = ccm.solve_path(At, Et, wt, g)
-    X2, L2, _, _ = ccm.solve_path(At, Et, wt, g)
-    assert torch.equal(X1, X2) and torch.equal(L1, L2)
+    for engine in (1, 2):
+        X1, L1, _, _ = ccm.solve_path(At, Et, wt, g, engine=engine)
+        X2, L2, _, _ = ccm.solve_path(At, Et, wt, g, engine=engine)
+        assert torch.equal(X1, X2) and torch.equal(L1, L2)
 
 
 def test_labels_entry_point(ccm):
