@@ -362,6 +362,9 @@ __device__ void b_solve(const BProb<Tc>& p, const BCommon& cm) {
     st.n_clusters = 0;
     st.kkt = st.eta_d = st.eta_p = st.gap = st.f_p = st.f_d = 0.0;
     double last_kkt = 1.0, last_etap = -1.0;
+    sigma = fmin(sigma, cm.sigma_max);  // a raised cap lasts one gamma
+    double cap = cm.sigma_max;
+    int at_cap = 0;
     double phi = 0.0, gn = 0.0, half_xa = 0.0;
     for (int outer = 0; outer < cm.max_outer; ++outer) {
       const double eps_in = fmax(0.5 * cm.tol, 0.1 * last_kkt);
@@ -515,7 +518,16 @@ __device__ void b_solve(const BProb<Tc>& p, const BCommon& cm) {
         st.status = CCM_OK;
         break;
       }
-      if (last_etap >= 0.0 && eta_p > 0.2 * last_etap) sigma = fmin(3.0 * sigma, cm.sigma_max);
+      // same penalty rule as the grid engine (cap rises 10x after 20 steps at it)
+      if (last_etap >= 0.0 && eta_p > 0.2 * last_etap) sigma = fmin(3.0 * sigma, cap);
+      if (sigma >= cap) {
+        if (++at_cap >= 20) {
+          cap = fmin(10.0 * cap, 1e6);
+          at_cap = 0;
+        }
+      } else {
+        at_cap = 0;
+      }
       last_etap = eta_p;
       last_kkt = st.kkt;
     }

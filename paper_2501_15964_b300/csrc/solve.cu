@@ -295,11 +295,27 @@ struct GridEngine {
       gamma_cur = gamma;
       ccm_stats st = {};
       double last_kkt = 1.0, last_etap = -1.0;
+      sigma = std::min(sigma, a.opt.sigma_max);  // a raised cap lasts one gamma
+      double cap = a.opt.sigma_max;
+      int at_cap = 0;
       bool converged = false;
       double gn = 0, phi = 0;
+      bool edge_ready = false;   // edge part of the evaluation at (X, U) already done
+      double edge_sigma = 0.0;   // ... with this penalty (by k_kkt_edge_eval)
       for (int outer = 0; outer < a.opt.max_outer; ++outer) {
         const double eps_in = std::max(0.5 * a.tol, 0.1 * last_kkt);
-        CCM_TRY(evaluate(X, &phi, &gn, nullptr));
+        if (edge_ready && edge_sigma == sigma) {
+          k_node_grad<L, CH, Tc><<<b_node, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind,
+                                                            sigma, d, G, Minv, n, ld, part, ctl);
+          CCM_COUNT(c);
+          CCM_CUDA(cudaGetLastError());
+          CCM_TRY(readback());
+          phi = hc->eval[1] + hc->eval[0] / sigma;
+          gn = std::sqrt(hc->eval[2]);
+        } else {
+          CCM_TRY(evaluate(X, &phi, &gn, nullptr));
+        }
+        edge_ready = false;
         for (int it = 0; it < a.opt.max_newton; ++it) {
           if (gn / scale <= eps_in) break;
           const double gr = gn / scale;
@@ -364,8 +380,12 @@ struct GridEngine {
         }
         // multiplier update: U <- Pi(U + sigma B X) (computed at the last evaluation)
         std::swap(U, Ut);
-        k_kkt_edge<L, CH><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, m, ld, part, ctl);
+        // KKT at (X, U) fused with the edge part of the next evaluation at (X, U)
+        k_kkt_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma, Ut,
+                                                              Yh, alpha, kind, m, ld, part, ctl);
         CCM_COUNT(c);
+        edge_ready = true;
+        edge_sigma = sigma;
         k_kkt_node<<<b_elem, threads, 0, s>>>(X, Ap, G, nl, part, ctl);
         CCM_COUNT(c);
         CCM_CUDA(cudaGetLastError());
@@ -386,7 +406,17 @@ struct GridEngine {
           converged = true;
           break;
         }
-        if (last_etap >= 0 && eta_p > 0.2 * last_etap) sigma = std::min(3.0 * sigma, a.opt.sigma_max);
+        // penalty: x3 while eta_p falls by less than 5x per step, up to a cap that
+        // starts at sigma_max and rises 10x after 20 outer steps spent at it
+        if (last_etap >= 0 && eta_p > 0.2 * last_etap) sigma = std::min(3.0 * sigma, cap);
+        if (sigma >= cap) {
+          if (++at_cap >= 20) {
+            cap = std::min(10.0 * cap, 1e6);
+            at_cap = 0;
+          }
+        } else {
+          at_cap = 0;
+        }
         last_etap = eta_p;
         last_kkt = st.kkt;
       }

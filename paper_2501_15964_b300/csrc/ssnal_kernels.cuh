@@ -94,12 +94,15 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
       for (int k = 0; k < 4; ++k) o[c][k] = scale * y[c][k];
     row_store<LANES, CH>(Ut + e * ld, ld, lane, o);
     if (kd == K_OUT) {
-      double inv = 1.0 / ny;
+      // yhat in the operator's precision: for float32 the scaling runs in
+      // float32 (FP64 throughput is the limit of this kernel)
+      const double inv = 1.0 / ny;
+      const Tc invc = (Tc)inv;
       Tc yh[CH][4];
 #pragma unroll
       for (int c = 0; c < CH; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)(y[c][k] * inv);
+        for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)y[c][k] * invc;
       row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
     }
   }
@@ -385,150 +388,6 @@ k_cg_update(Tc* __restrict__ Dx, const Tc* __restrict__ P, Tc* __restrict__ R,
   }
 }
 
-// Same operator as k_cg_matvec for wide rows (one warp per node, CH quads per
-// lane, CH >= 4): instead of holding the neighbour rows in registers, every
-// edge is streamed twice, quad by quad -- a dot sweep (s = yhat . v) and an
-// update sweep (acc += alpha (v - s yhat)) whose loads hit L1 -- and the own row
-// p_i lives in shared memory. Only the accumulator row stays in registers, so
-// four times more warps fit per SM and more rows are in flight. Summation
-// order per element is identical to k_cg_matvec.
-template <int CH, typename Tc>
-__global__ void __launch_bounds__(256, 2)
-k_cg_matvec_stream(const Tc* __restrict__ Pold, Tc* __restrict__ Pnew, const Tc* __restrict__ R,
-                   const Tc* __restrict__ Minv, const Tc* __restrict__ Dg, Tc* __restrict__ Q,
-                   const Tc* __restrict__ Yh, const Tc* __restrict__ alpha,
-                   const uint8_t* __restrict__ kind, const int64_t* __restrict__ off,
-                   const int2* __restrict__ inc, double sigma, int64_t n, int ld,
-                   double* partials, Ctl* ctl) {
-  if (!ctl->cg.active) return;
-  extern __shared__ __align__(16) unsigned char smem_mv[];
-  const Tc beta = (Tc)ctl->cg.beta;
-  const bool use_old = ctl->cg.beta != 0.0;
-  const int lane = threadIdx.x & 31;
-  Tc* sp = reinterpret_cast<Tc*>(smem_mv) + (size_t)(threadIdx.x >> 5) * ld;  // own row
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t ng = (int64_t)gridDim.x * blockDim.x >> 5;
-  const Tc sg = (Tc)sigma;
-  double acc[1] = {0.0};
-  for (int64_t i = g0; i < n; i += ng) {
-    const Tc mi = Minv[i];
-    __syncwarp();
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int q = c * 32 + lane;
-      if (4 * q < ld) {
-        Tc r[4], po[4];
-        Vec4<Tc>::load(R + i * ld + 4 * q, r);
-        if (use_old) Vec4<Tc>::load(Pold + i * ld + 4 * q, po);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) r[k] = mi * r[k] + (use_old ? beta * po[k] : (Tc)0);
-        Vec4<Tc>::store(sp + 4 * q, r);
-        Vec4<Tc>::store(Pnew + i * ld + 4 * q, r);
-      }
-    }
-    __syncwarp();
-    Tc av[CH][4];
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) av[c][k] = (Tc)0;
-    const int64_t b = off[i], eend = off[i + 1];
-    int2 eo_n = make_int2(0, 0);
-    uint8_t kd_n = K_INERT;
-    Tc mo_n = (Tc)0, a_n = (Tc)0;
-    if (b < eend) {
-      eo_n = inc[b];
-      kd_n = kind[eo_n.x];
-      mo_n = Minv[eo_n.y];
-      a_n = alpha[eo_n.x];
-    }
-    for (int64_t t = b; t < eend; ++t) {
-      const int2 eo = eo_n;
-      const uint8_t kd = kd_n;
-      const Tc mo = mo_n, a = a_n;
-      if (t + 1 < eend) {
-        eo_n = inc[t + 1];
-        kd_n = kind[eo_n.x];
-        mo_n = Minv[eo_n.y];
-        a_n = alpha[eo_n.x];
-      }
-      if (kd == K_INERT) continue;
-      const Tc* Ro = R + (int64_t)eo.y * ld;
-      const Tc* Po = Pold + (int64_t)eo.y * ld;
-      const Tc* Y = Yh + (int64_t)eo.x * ld;
-      Tc s = (Tc)0;
-      if (kd == K_OUT) {
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int q = c * 32 + lane;
-          if (4 * q < ld) {
-            Tc r[4], po[4], y[4], pi[4];
-            Vec4<Tc>::load(Ro + 4 * q, r);
-            if (use_old) Vec4<Tc>::load(Po + 4 * q, po);
-            Vec4<Tc>::load(Y + 4 * q, y);
-            Vec4<Tc>::load(sp + 4 * q, pi);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              s += y[k] * (pi[k] - (mo * r[k] + (use_old ? beta * po[k] : (Tc)0)));
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      }
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int q = c * 32 + lane;
-        if (4 * q < ld) {
-          Tc r[4], po[4], pi[4];
-          Vec4<Tc>::load(Ro + 4 * q, r);
-          if (use_old) Vec4<Tc>::load(Po + 4 * q, po);
-          Vec4<Tc>::load(sp + 4 * q, pi);
-          if (kd == K_OUT) {
-            Tc y[4];
-            Vec4<Tc>::load(Y + 4 * q, y);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const Tc v = pi[k] - (mo * r[k] + (use_old ? beta * po[k] : (Tc)0));
-              av[c][k] += a * (v - s * y[k]);
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              av[c][k] += pi[k] - (mo * r[k] + (use_old ? beta * po[k] : (Tc)0));
-          }
-        }
-      }
-    }
-    const Tc di = Dg ? Dg[i] : (Tc)1;
-    Tc dot = (Tc)0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int q = c * 32 + lane;
-      if (4 * q < ld) {
-        Tc pi[4];
-        Vec4<Tc>::load(sp + 4 * q, pi);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          av[c][k] = di * pi[k] + sg * av[c][k];
-          dot += pi[k] * av[c][k];
-        }
-        Vec4<Tc>::store(Q + i * ld + 4 * q, av[c]);
-      }
-    }
-    acc[0] += (double)dot;
-  }
-  double tot[1];
-  if (grid_reduce<1>(acc, partials, &ctl->counter[C_MV], tot) && threadIdx.x == 0) {
-    CgCtl& c = ctl->cg;
-    if (tot[0] > 0.0 && isfinite(tot[0])) {
-      c.alpha = c.rz / tot[0];
-    } else {
-      c.alpha = 0.0;
-      c.active = 0;
-    }
-  }
-}
-
 // ------------------------------------------------------------ line search
 // Xt = X + t Dx; gd = <G, Dx>.
 template <typename Tc>
@@ -604,6 +463,95 @@ k_kkt_edge(const double* __restrict__ X, const double* __restrict__ U,
   }
 }
 
+// KKT edge pass fused with the next evaluation at the same (X, U): per edge
+// bx = x_i - x_j feeds both the prox residual / r||bx|| (as k_kkt_edge) and
+// y = u + sigma bx with its kind, alpha, yhat, Pi(y) and h (as k_edge_eval).
+template <int LANES, int CH, typename Tc>
+__global__ void __launch_bounds__(256)
+k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
+                const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
+                double sigma, double* __restrict__ Ut, Tc* __restrict__ Yh,
+                Tc* __restrict__ alpha, uint8_t* __restrict__ kind, int64_t m, int ld,
+                double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // ||res||^2, sum r||bx||, sum h, #outside
+  for (int64_t e = g0; e < m; e += ng) {
+    const int2 ij = edges[e];
+    const double r = gamma * w[e];
+    double bx[CH][4], u[CH][4], y[CH][4];
+    row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, bx);
+    row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, y);
+    row_load<LANES, CH>(U + e * ld, ld, lane, u);
+    double sb = 0.0, sv = 0.0, ss = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        bx[c][k] -= y[c][k];
+        sb = fma(bx[c][k], bx[c][k], sb);
+        const double v = u[c][k] + bx[c][k];
+        sv = fma(v, v, sv);
+        y[c][k] = fma(sigma, bx[c][k], u[c][k]);
+        ss = fma(y[c][k], y[c][k], ss);
+      }
+    sb = group_sum<LANES>(sb, mask);
+    sv = group_sum<LANES>(sv, mask);
+    ss = group_sum<LANES>(ss, mask);
+    const double nv = sqrt(sv);
+    const double shrink = (nv > r) ? 1.0 - r / nv : 0.0;
+    double sres = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double res = bx[c][k] - shrink * (u[c][k] + bx[c][k]);
+        sres = fma(res, res, sres);
+      }
+    acc[0] += sres;
+    const double ny = sqrt(ss);
+    uint8_t kd;
+    double scale, a;
+    if (!(r > 0.0)) {
+      kd = K_INERT; scale = 0.0; a = 0.0;
+    } else if (ny <= r) {
+      kd = K_IN; scale = 1.0; a = 1.0;
+    } else {
+      kd = K_OUT; scale = r / ny; a = r / ny;
+    }
+    if (lane == 0) {
+      acc[1] += r * sqrt(sb);
+      acc[2] += (ny <= r) ? 0.5 * ss : r * ny - 0.5 * r * r;
+      acc[3] += (kd == K_OUT) ? 1.0 : 0.0;
+      kind[e] = kd;
+      alpha[e] = (Tc)a;
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) u[c][k] = scale * y[c][k];
+    row_store<LANES, CH>(Ut + e * ld, ld, lane, u);
+    if (kd == K_OUT) {
+      const Tc invc = (Tc)(1.0 / ny);
+      Tc yh[CH][4];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)y[c][k] * invc;
+      row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
+    }
+  }
+  double tot[4];
+  if (grid_reduce<4>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {
+    ctl->kkt[0] = tot[0];
+    ctl->kkt[1] = tot[1];
+    ctl->eval[0] = tot[2];
+    ctl->eval[3] = tot[3];
+  }
+}
+
 // Per node: B^T U = G - (X - A); <A, B^T U>, ||B^T U||^2.
 __global__ void __launch_bounds__(256)
 k_kkt_node(const double* __restrict__ X, const double* __restrict__ Ap,
@@ -617,33 +565,14 @@ __global__ void k_unpad_rows(const double* __restrict__ src, double* __restrict_
 
 static constexpr int kMaxPartBlocksPerSm = 8;  // partial-sum slots per SM
 
-// Newton-CG operator launch: rows of up to 128 elements per lane-group hold
-// the neighbour rows in registers (k_cg_matvec); wider rows (one warp, 4+
-// quads per lane) stream them twice through L1 (k_cg_matvec_stream).
+// Newton-CG operator launch (grid sized to the node groups, at most 4 blocks per SM).
 template <int L, int CH, typename Tc>
 inline int launch_matvec(Ctx* c, const Tc* Pold, Tc* Pnew, const Tc* R, const Tc* Minv, const Tc* Dg,
                   Tc* Q, const Tc* Yh, const Tc* alpha, const uint8_t* kind, const int64_t* off,
                   const int2* inc, double sigma, int64_t n, int ld, double* part, Ctl* ctl,
                   cudaStream_t s) {
   const int threads = 256;
-  if constexpr (L == 32 && CH >= 4) {
-    const size_t smem = (size_t)(threads / 32) * ld * sizeof(Tc);
-    static int configured = 0;
-    if (!configured) {
-      CCM_CUDA(cudaFuncSetAttribute(k_cg_matvec_stream<CH, Tc>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      configured = 1;
-    }
-    int occ = 0;
-    CCM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_matvec_stream<CH, Tc>,
-                                                           threads, smem));
-    occ = std::max(1, std::min(occ, kMaxPartBlocksPerSm));
-    const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n + threads / 32 - 1) / (threads / 32), (int64_t)c->num_sms * occ));
-    k_cg_matvec_stream<CH, Tc><<<blocks, threads, smem, s>>>(Pold, Pnew, R, Minv, Dg, Q, Yh, alpha,
-                                                             kind, off, inc, sigma, n, ld, part,
-                                                             ctl);
-  } else {
+  {
     const int gpb = threads / L;
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
