@@ -161,6 +161,28 @@ int ccm_labels(ccm_ctx* ctx, const double* X, int64_t n, int32_t d, const int32_
                int64_t m, int32_t* labels, int32_t* n_clusters, ccm_stream_t stream);
 
 /*
+ * ccm_labels_noalloc - ccm_labels for callers that cannot allocate device
+ * memory. The paper has no counterpart; this is a deployment variant.
+ *
+ * Some callers must not call cudaMalloc or cudaFree: code running under a
+ * memory pool or allocator that owns all device memory, hosts that reserve the
+ * device memory up front, or callers that cannot afford the implicit
+ * synchronisation an allocation may bring. This entry point needs no context and
+ * allocates nothing: its scratch is a fixed static device array of 262,144
+ * nodes (about 2 MB, kept by every GPU that loads libccm until the process exits).
+ * The caller still passes X (n x d), the edges (m x 2) and labels (n int32), all
+ * device pointers; *n_clusters (host, may be NULL) receives the cluster count.
+ * n above 262,144 returns CCM_ERR_INVALID_ARG with a message naming the limit.
+ * The first call on a device (with that device current) looks up the scratch
+ * address with cudaGetSymbolAddress: make that first call before any stream
+ * capture. All calls share the one scratch array, so calls that can overlap on
+ * the GPU (different streams or host threads) race: serialise them. The call
+ * synchronises `stream` before returning.
+ */
+int ccm_labels_noalloc(const double* X, int64_t n, int32_t d, const int32_t* edges, int64_t m,
+                       int32_t* labels, int32_t* n_clusters, ccm_stream_t stream);
+
+/*
  * ccm_path_vjp - vector-Jacobian product of the path (not in the paper):
  * given G_t = dL/dX*(gamma_t) (T x n x d), returns
  *     dLdA = sum_t dL_t/dA  (n x d)   and   dLdw = sum_t dL_t/dw  (m),
