@@ -365,9 +365,10 @@ __device__ void b_solve(const BProb<Tc>& p, const BCommon& cm) {
     sigma = fmin(sigma, cm.sigma_max);  // a raised cap lasts one gamma
     double cap = cm.sigma_max;
     int at_cap = 0;
+    double eps_gap = 1.0;  // inner-tolerance cap from the duality gap
     double phi = 0.0, gn = 0.0, half_xa = 0.0;
     for (int outer = 0; outer < cm.max_outer; ++outer) {
-      const double eps_in = fmax(0.5 * cm.tol, 0.1 * last_kkt);
+      const double eps_in = fmin(fmax(0.5 * cm.tol, 0.1 * last_kkt), eps_gap);
       double ev[2], nv[2];
       b_edge_eval<L, CH, Tc>(p, X, U, Ut, gamma, sigma, ld, ev);
       b_node_grad<L, CH, Tc>(p, X, Ut, sigma, d, ld, nv);
@@ -518,6 +519,9 @@ __device__ void b_solve(const BProb<Tc>& p, const BCommon& cm) {
         st.status = CCM_OK;
         break;
       }
+      // f_p - f_d >= 1/2 ||X - A + B^T U||^2 (U dual feasible): cap the inner tolerance
+      if (gap > cm.tol)
+        eps_gap = fmin(eps_gap, 0.5 * sqrt(2.0 * cm.tol * (1.0 + fabs(fp) + fabs(fd))) / scale);
       // same penalty rule as the grid engine (cap rises 10x after 20 steps at it)
       if (last_etap >= 0.0 && eta_p > 0.2 * last_etap) sigma = fmin(3.0 * sigma, cap);
       if (sigma >= cap) {

@@ -123,6 +123,21 @@ __global__ void k_sort_inc(const int64_t* __restrict__ off, int2* __restrict__ i
   }
 }
 
+__global__ void k_warp_partition(const int64_t* __restrict__ off, int64_t n, int nwg,
+                                 int* __restrict__ part) {
+  const int64_t total = off[n] + 2 * n;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w <= nwg; w += gridDim.x * blockDim.x) {
+    const int64_t target = total * (int64_t)w / nwg;
+    int64_t lo = 0, hi = n;  // first i with off[i] + 2i >= target
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (off[mid] + 2 * mid >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    part[w] = (int)lo;
+  }
+}
+
 int check_edges(Ctx* c, const int2* edges, int64_t m, int64_t n, const double* w,
                 cudaStream_t s) {
   void* pb;
@@ -193,7 +208,6 @@ struct GridEngine {
       return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, maxb));
     };
     const int b_edge = (int)std::max<int64_t>(1, std::min<int64_t>((m + gpb - 1) / gpb, maxb));
-    const int b_node = (int)std::max<int64_t>(1, std::min<int64_t>((n + gpb - 1) / gpb, maxb));
     const int b_elem = nb(nl);
     const int b_quad = nb((nl + 3) / 4);
 
@@ -205,9 +219,11 @@ struct GridEngine {
     CCM_TRY(get(S_G, nl * 8, &p)); double* G = (double*)p;
     CCM_TRY(get(S_DX, nl * sizeof(Tc), &p)); Tc* Dx = (Tc*)p;
     CCM_TRY(get(S_R, nl * sizeof(Tc), &p)); Tc* R = (Tc*)p;
-    CCM_TRY(get(S_P0, nl * sizeof(Tc), &p)); Tc* P0 = (Tc*)p;
-    CCM_TRY(get(S_P1, nl * sizeof(Tc), &p)); Tc* P1 = (Tc*)p;
-    CCM_TRY(get(S_Q, nl * sizeof(Tc), &p)); Tc* Q = (Tc*)p;
+    CCM_TRY(get(S_P0, nl * sizeof(Tc), &p)); Tc* P = (Tc*)p;    // CG search direction
+    CCM_TRY(get(S_P1, nl * sizeof(Tc), &p)); Tc* Sv = (Tc*)p;   // S = V P
+    CCM_TRY(get(S_Q, nl * sizeof(Tc), &p)); Tc* W = (Tc*)p;     // W = V M R
+    CCM_TRY(get(S_META, std::max<int64_t>(2 * m, 1) * sizeof(IncMeta<Tc>), &p));
+    IncMeta<Tc>* meta = (IncMeta<Tc>*)p;
     CCM_TRY(get(S_MINV, n * sizeof(Tc), &p)); Tc* Minv = (Tc*)p;
     CCM_TRY(get(S_U, std::max<int64_t>(ml, 1) * 8, &p)); double* Ua = (double*)p;
     CCM_TRY(get(S_UT, std::max<int64_t>(ml, 1) * 8, &p)); double* Ub = (double*)p;
@@ -225,6 +241,17 @@ struct GridEngine {
     int64_t* off;
     int2* inc;
     CCM_TRY(build_csr(c, edges, m, n, &off, &inc, s));
+    // long rows: the bulk-copy operator, one node range per warp
+    const TmaShape tsh = L == 32 ? tma_shape<Tc>(ld) : TmaShape{};
+    const TmaShape gsh = grad_shape(tsh, ld);
+    int* wpart = nullptr;
+    if (tsh.nw > 0) {
+      const int nwg = c->num_sms * tsh.nw;
+      CCM_TRY(get(S_WPART, (size_t)(nwg + 1) * sizeof(int), &p));
+      wpart = (int*)p;
+      k_warp_partition<<<(nwg + 256) / 256, 256, 0, s>>>(off, n, nwg, wpart);
+      CCM_COUNT(c);
+    }
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     k_pad_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld);
     CCM_COUNT(c);
@@ -248,6 +275,10 @@ struct GridEngine {
     auto readback = [&]() -> int {
       CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
       CCM_CUDA(cudaStreamSynchronize(s));
+      if (hc->fault) {
+        set_error("ccm_solve_path: a bounded device-side wait timed out");
+        return CCM_ERR_TIMEOUT;
+      }
       return CCM_OK;
     };
     CCM_TRY(readback());
@@ -279,9 +310,8 @@ struct GridEngine {
       k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
                                                         Ut, Yh, alpha, kind, m, ld, part, ctl);
       CCM_COUNT(c);
-      k_node_grad<L, CH, Tc><<<b_node, threads, 0, s>>>(Xc, Ap, Ut, off, inc, alpha, kind, sigma,
-                                                        d, G, Minv, n, ld, part, ctl);
-      CCM_COUNT(c);
+      CCM_TRY(launch_node_grad<L, CH, Tc>(c, Xc, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv,
+                                          wpart, gsh, n, ld, part, ctl, s));
       CCM_CUDA(cudaGetLastError());
       CCM_TRY(readback());
       *phi = hc->eval[1] + hc->eval[0] / sigma;
@@ -298,16 +328,16 @@ struct GridEngine {
       sigma = std::min(sigma, a.opt.sigma_max);  // a raised cap lasts one gamma
       double cap = a.opt.sigma_max;
       int at_cap = 0;
+      double eps_gap = 1.0;      // inner-tolerance cap from the duality gap (below)
       bool converged = false;
       double gn = 0, phi = 0;
       bool edge_ready = false;   // edge part of the evaluation at (X, U) already done
       double edge_sigma = 0.0;   // ... with this penalty (by k_kkt_edge_eval)
       for (int outer = 0; outer < a.opt.max_outer; ++outer) {
-        const double eps_in = std::max(0.5 * a.tol, 0.1 * last_kkt);
+        const double eps_in = std::min(std::max(0.5 * a.tol, 0.1 * last_kkt), eps_gap);
         if (edge_ready && edge_sigma == sigma) {
-          k_node_grad<L, CH, Tc><<<b_node, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind,
-                                                            sigma, d, G, Minv, n, ld, part, ctl);
-          CCM_COUNT(c);
+          CCM_TRY(launch_node_grad<L, CH, Tc>(c, X, Ap, Ut, off, inc, alpha, kind, sigma, d, G,
+                                              Minv, wpart, gsh, n, ld, part, ctl, s));
           CCM_CUDA(cudaGetLastError());
           CCM_TRY(readback());
           phi = hc->eval[1] + hc->eval[0] / sigma;
@@ -321,21 +351,18 @@ struct GridEngine {
           const double gr = gn / scale;
           const double eta = std::min(0.1, std::max(tc_floor, std::sqrt(gr)));
           k_cg_init<Tc><<<b_elem, threads, 0, s>>>(G, Minv, R, Dx, n, ld, eta, a.opt.max_cg,
-                                                   part, ctl);
+                                                   inc, kind, alpha, meta, 2 * m, part, ctl);
           CCM_COUNT(c);
           CCM_CUDA(cudaGetLastError());
-          Tc* Pa = P0;
-          Tc* Pb = P1;
           int it_before = 0;
           for (int chunk = 0; chunk * CHUNK < a.opt.max_cg; ++chunk) {
             for (int k = 0; k < CHUNK; ++k) {
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k], s));
-              CCM_TRY(launch_matvec<L, CH, Tc>(c, Pa, Pb, R, Minv, nullptr, Q, Yh, alpha, kind,
-                                                off, inc, sigma, n, ld, part, ctl, s));
+              CCM_TRY(launch_matvec<L, CH, Tc>(c, R, Minv, nullptr, W, Yh, meta, off, inc, wpart,
+                                                tsh, sigma, n, ld, part, ctl, s));
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k + 1], s));
-              k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, Pb, R, Q, Minv, n, ld, part, ctl);
+              k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, P, Sv, R, W, Minv, n, ld, part, ctl);
               CCM_COUNT(c);
-              std::swap(Pa, Pb);
             }
             CCM_CUDA(cudaGetLastError());
             CCM_TRY(readback());
@@ -346,8 +373,7 @@ struct GridEngine {
                 CCM_CUDA(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
                 profile.matvec_ms_total += ms;
                 profile.matvec_launches += 1;
-                profile.matvec_bytes_total += a.matvec_bytes(hc->eval[3], k > 0 || chunk > 0,
-                                                             sizeof(Tc));
+                profile.matvec_bytes_total += a.matvec_bytes(hc->eval[3], sizeof(Tc));
               }
             }
             it_before = hc->cg.it;
@@ -406,6 +432,11 @@ struct GridEngine {
           converged = true;
           break;
         }
+        // f_p - f_d >= 1/2 ||X - A + B^T U||^2 for dual-feasible U, so a gap above
+        // tol caps the inner tolerance at half the gradient norm that allows it
+        if (gap > a.tol)
+          eps_gap = std::min(eps_gap, 0.5 * std::sqrt(2.0 * a.tol * (1.0 + std::fabs(fp) +
+                                                                     std::fabs(fd))) / scale);
         // penalty: x3 while eta_p falls by less than 5x per step, up to a cap that
         // starts at sigma_max and rises 10x after 20 outer steps spent at it
         if (last_etap >= 0 && eta_p > 0.2 * last_etap) sigma = std::min(3.0 * sigma, cap);

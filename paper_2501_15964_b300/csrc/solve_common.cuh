@@ -23,14 +23,13 @@ struct SolveArgs {
   const double* U0 = nullptr;
 
   // Algorithmic bytes of one Newton-CG operator launch (each datum once):
-  // R and (after the first iteration) P_old read, P_new and Q written
-  // (n x ld each), Minv (n), yhat rows and alpha of the m_out outside edges,
-  // kind (m bytes), CSR offsets (n+1 int64) and incidences (2m int2).
-  double matvec_bytes(double m_out, bool with_pold, size_t tcb) const {
+  // R read and W written (n x ld each), Minv (n), the yhat rows of the m_out
+  // outside edges, the packed incidence coefficients (2m x 2 elements), the
+  // CSR incidences (2m int2) and offsets (n+1 int64).
+  double matvec_bytes(double m_out, size_t tcb) const {
     const double ld = (double)((d + 3) / 4 * 4);
-    const double vec = (double)n * ld * (double)tcb;
-    return vec * (with_pold ? 4.0 : 3.0) + (double)n * tcb + m_out * (ld + 1.0) * tcb +
-           (double)m + 8.0 * (double)(n + 1) + 16.0 * (double)m;
+    return 2.0 * (double)n * ld * (double)tcb + (double)n * tcb + m_out * ld * tcb +
+           2.0 * (double)m * (8.0 + 2.0 * tcb) + 8.0 * (double)(n + 1);
   }
 };
 

@@ -264,6 +264,8 @@ static int run_vjp(Ctx* c, const double* A, int64_t n, int d, const int2* edges,
   double* Minv = Dg + n;
   CCM_TRY(ws_get(c, S_PART, (size_t)kMaxPartBlocksPerSm * c->num_sms * 4 * 8, &p));
   double* part = (double*)p;
+  CCM_TRY(ws_get(c, S_META, (size_t)std::max<int64_t>(2 * m2, 1) * sizeof(IncMeta<double>), &p));
+  IncMeta<double>* meta = (IncMeta<double>*)p;
   CCM_TRY(ws_get(c, S_CTRL, sizeof(Ctl), &p));
   Ctl* ctl = (Ctl*)p;
   void* hp;
@@ -318,18 +320,18 @@ static int run_vjp(Ctx* c, const double* A, int64_t n, int d, const int2* edges,
     const int b_elem = nb((int64_t)K * ld);
     const int b_quad = nb(((int64_t)K * ld + 3) / 4);
     const int maxit = 5000;
-    k_cg_init<double><<<b_elem, threads, 0, s>>>(bneg, Minv, R, lam, K, ld, 1e-11, maxit, part,
-                                                 ctl);
+    k_cg_init<double><<<b_elem, threads, 0, s>>>(bneg, Minv, R, lam, K, ld, 1e-11, maxit, cinc,
+                                                 kind, coef, meta, nvalid, part, ctl);
     CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
     const int CHUNK = 16;
     for (int chunk = 0; chunk * CHUNK < maxit; ++chunk) {
       for (int k = 0; k < CHUNK; ++k) {
-        CCM_TRY(launch_matvec<L, CH, double>(c, Pa, Pb, R, Minv, Dg, Qv, S, coef, kind, coff,
-                                             cinc, 1.0, K, ld, part, ctl, s));
-        k_cg_update<double><<<b_quad, threads, 0, s>>>(lam, Pb, R, Qv, Minv, K, ld, part, ctl);
+        CCM_TRY(launch_matvec<L, CH, double>(c, R, Minv, Dg, Qv, S, meta, coff, cinc, nullptr,
+                                             TmaShape{}, 1.0, K, ld, part, ctl, s));
+        k_cg_update<double><<<b_quad, threads, 0, s>>>(lam, Pa, Pb, R, Qv, Minv, K, ld, part,
+                                                       ctl);
         CCM_COUNT(c);
-        std::swap(Pa, Pb);
       }
       CCM_CUDA(cudaGetLastError());
       CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
