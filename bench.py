@@ -377,7 +377,8 @@ def main():
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                         "launches_timed": int(mv_n), "traffic": None},
+                         "launches_timed": int(mv_n),
+                         "ms_per_step": mv_ms / args.steps, "traffic": None},
             "e2e": {"value": e2e, "unit": "gamma-solves/s",
                     "h2d_bytes_per_step": int(A.nbytes),
                     "d2h_bytes_per_step": int(X_host.numel() * 8 + L_host.numel() * 4)},

@@ -158,9 +158,12 @@ __device__ __forceinline__ unsigned group_mask() {
 // partial per quantity; the last block to arrive (counter) sums the partials
 // in block order and returns true with the totals in `tot` (all its threads).
 // The counter is reset by that block, so kernels can be relaunched.
+// `nextra` further partial rows (indices gridDim.x .. gridDim.x + nextra - 1,
+// written before their writers' blocks arrive) join the final sum in index order.
 template <int NRED>
 __device__ __forceinline__ bool grid_reduce(double (&acc)[NRED], double* partials,
-                                            unsigned* counter, double (&tot)[NRED]) {
+                                            unsigned* counter, double (&tot)[NRED],
+                                            int nextra = 0) {
   __shared__ double sh[32][NRED];
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -194,7 +197,7 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NRED], double* partial
 #pragma unroll
   for (int k = 0; k < NRED; ++k) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int b = threadIdx.x; b < (int)gridDim.x + nextra; b += blockDim.x)
       v += __ldcg(partials + (size_t)b * NRED + k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -11,6 +11,7 @@
 
 #include "ccm_internal.cuh"
 #include "solve_common.cuh"
+#include "ring_kernels.cuh"
 #include "ssnal_kernels.cuh"
 
 namespace ccm {
@@ -123,18 +124,52 @@ __global__ void k_sort_inc(const int64_t* __restrict__ off, int2* __restrict__ i
   }
 }
 
-__global__ void k_warp_partition(const int64_t* __restrict__ off, int64_t n, int nwg,
-                                 int* __restrict__ part) {
-  const int64_t total = off[n] + 2 * n;
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w <= nwg; w += gridDim.x * blockDim.x) {
-    const int64_t target = total * (int64_t)w / nwg;
-    int64_t lo = 0, hi = n;  // first i with off[i] + 2i >= target
+__global__ void k_span_setup(const int64_t* __restrict__ off, int64_t n, int nwg,
+                             WarpSpan* __restrict__ spans) {
+  const int64_t U = off[n] + n;
+  auto node_of = [&](int64_t u) {  // largest i with off[i] + i <= u
+    int64_t lo = 0, hi = n - 1;
     while (lo < hi) {
-      const int64_t mid = (lo + hi) / 2;
-      if (off[mid] + 2 * mid >= target) hi = mid;
-      else lo = mid + 1;
+      const int64_t mid = (lo + hi + 1) / 2;
+      if (off[mid] + mid <= u) lo = mid;
+      else hi = mid - 1;
     }
-    part[w] = (int)lo;
+    return (int)lo;
+  };
+  auto warp_of = [&](int64_t u) {  // largest w with U w / nwg <= u
+    int lo = 0, hi = nwg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (U * mid / nwg <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  };
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwg; w += gridDim.x * blockDim.x) {
+    WarpSpan sp;
+    sp.ub = U * w / nwg;
+    sp.ue = U * (w + 1) / nwg;
+    auto parts = [&](int wf, int wl) {  // non-empty spans among warps wf..wl
+      int np = 0;
+      for (int v = wf; v <= wl; ++v) np += (U * v / nwg < U * (v + 1) / nwg) ? 1 : 0;
+      return np;
+    };
+    if (sp.ub >= sp.ue) {
+      sp.i0 = 0;
+      sp.i1 = -1;
+      sp.wf0 = sp.wl0 = sp.wf1 = sp.wl1 = w;
+      sp.np0 = sp.np1 = 1;
+    } else {
+      sp.i0 = node_of(sp.ub);
+      sp.i1 = node_of(sp.ue - 1);
+      sp.wf0 = warp_of(off[sp.i0] + sp.i0);
+      sp.wl0 = warp_of(off[sp.i0 + 1] + sp.i0);
+      sp.np0 = parts(sp.wf0, sp.wl0);
+      sp.wf1 = warp_of(off[sp.i1] + sp.i1);
+      sp.wl1 = warp_of(off[sp.i1 + 1] + sp.i1);
+      sp.np1 = parts(sp.wf1, sp.wl1);
+    }
+    spans[w] = sp;
   }
 }
 
@@ -241,16 +276,27 @@ struct GridEngine {
     int64_t* off;
     int2* inc;
     CCM_TRY(build_csr(c, edges, m, n, &off, &inc, s));
-    // long rows: the bulk-copy operator, one node range per warp
-    const TmaShape tsh = L == 32 ? tma_shape<Tc>(ld) : TmaShape{};
-    const TmaShape gsh = grad_shape(tsh, ld);
-    int* wpart = nullptr;
-    if (tsh.nw > 0) {
-      const int nwg = c->num_sms * tsh.nw;
-      CCM_TRY(get(S_WPART, (size_t)(nwg + 1) * sizeof(int), &p));
-      wpart = (int*)p;
-      k_warp_partition<<<(nwg + 256) / 256, 256, 0, s>>>(off, n, nwg, wpart);
-      CCM_COUNT(c);
+    // long rows: the shared-memory ring kernels over an even split of the
+    // incidence stream (one span per warp)
+    RingPlan rp;
+    if (L == 32) {
+      rp.sh = ring_shape<Tc>(ld);
+      if (rp.sh.nw > 0) {
+        rp.nwg = c->num_sms * rp.sh.nw;
+        const size_t b_sp = round_up((int64_t)rp.nwg * sizeof(WarpSpan), 256);
+        const size_t b_cnt = round_up((int64_t)rp.nwg * 4, 256);
+        const size_t b_pd = round_up((int64_t)rp.nwg * 2 * 8, 256);
+        const size_t b_parts = (size_t)rp.nwg * 2 * ld * 8;
+        CCM_TRY(get(S_WPART, b_sp + b_cnt + b_pd + b_parts, &p));
+        char* base = (char*)p;
+        rp.spans = (WarpSpan*)base;
+        rp.cnt = (unsigned*)(base + b_sp);
+        rp.pdiag = (double*)(base + b_sp + b_cnt);
+        rp.parts = base + b_sp + b_cnt + b_pd;
+        CCM_CUDA(cudaMemsetAsync(rp.cnt, 0, b_cnt, s));
+        k_span_setup<<<(rp.nwg + 255) / 256, 256, 0, s>>>(off, n, rp.nwg, rp.spans);
+        CCM_COUNT(c);
+      }
     }
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     k_pad_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld);
@@ -311,7 +357,7 @@ struct GridEngine {
                                                         Ut, Yh, alpha, kind, m, ld, part, ctl);
       CCM_COUNT(c);
       CCM_TRY(launch_node_grad<L, CH, Tc>(c, Xc, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv,
-                                          wpart, gsh, n, ld, part, ctl, s));
+                                          rp, n, ld, part, ctl, s));
       CCM_CUDA(cudaGetLastError());
       CCM_TRY(readback());
       *phi = hc->eval[1] + hc->eval[0] / sigma;
@@ -337,7 +383,7 @@ struct GridEngine {
         const double eps_in = std::min(std::max(0.5 * a.tol, 0.1 * last_kkt), eps_gap);
         if (edge_ready && edge_sigma == sigma) {
           CCM_TRY(launch_node_grad<L, CH, Tc>(c, X, Ap, Ut, off, inc, alpha, kind, sigma, d, G,
-                                              Minv, wpart, gsh, n, ld, part, ctl, s));
+                                              Minv, rp, n, ld, part, ctl, s));
           CCM_CUDA(cudaGetLastError());
           CCM_TRY(readback());
           phi = hc->eval[1] + hc->eval[0] / sigma;
@@ -358,8 +404,8 @@ struct GridEngine {
           for (int chunk = 0; chunk * CHUNK < a.opt.max_cg; ++chunk) {
             for (int k = 0; k < CHUNK; ++k) {
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k], s));
-              CCM_TRY(launch_matvec<L, CH, Tc>(c, R, Minv, nullptr, W, Yh, meta, off, inc, wpart,
-                                                tsh, sigma, n, ld, part, ctl, s));
+              CCM_TRY(launch_matvec<L, CH, Tc>(c, R, Minv, nullptr, W, Yh, meta, off, inc, rp,
+                                                sigma, n, ld, part, ctl, s));
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k + 1], s));
               k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, P, Sv, R, W, Minv, n, ld, part, ctl);
               CCM_COUNT(c);

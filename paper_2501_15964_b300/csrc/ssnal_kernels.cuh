@@ -17,7 +17,6 @@
 #pragma once
 
 #include "ccm_internal.cuh"
-#include "tma.cuh"
 
 namespace ccm {
 
@@ -188,164 +187,6 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
   }
 }
 
-// Node gradient for long rows (LANES = 32): one warp per node over the
-// contiguous node ranges of wpart (as the bulk-copy operator). Lane 0 streams
-// the Ut row of every non-inert incidence into a per-warp ring of shared-memory
-// slots with 1-D bulk copies (one mbarrier per slot); the slot metadata carries
-// the other endpoint (for the sign: + when node i is the first endpoint) and
-// trace(P_l)/d. Sums run in increasing edge id, as in k_node_grad.
-struct GradMeta {
-  double t;   // trace(P_l)/d
-  int other;  // other endpoint of the incidence
-  int live;   // 0: inert edge (no row copied)
-};
-
-template <int CH, typename Tc>
-__global__ void __launch_bounds__(256, 1)
-k_node_grad_tma(const double* __restrict__ X, const double* __restrict__ Ap,
-                const double* __restrict__ Ut, const int64_t* __restrict__ off,
-                const int2* __restrict__ inc, const Tc* __restrict__ alpha,
-                const uint8_t* __restrict__ kind, double sigma, int d, double* __restrict__ G,
-                Tc* __restrict__ Minv, const int* __restrict__ wpart, int64_t n, int ld,
-                int stages, double* partials, Ctl* ctl) {
-  constexpr int LANES = 32;
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * nw + warp;
-  const uint32_t rowb = (uint32_t)ld * 8u;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * stages;
-  GradMeta* smeta = reinterpret_cast<GradMeta*>(smem + (size_t)nw * stages * 8) +
-                    (size_t)warp * stages;
-  double* ring = reinterpret_cast<double*>(smem + tma_ring_header(nw, stages, sizeof(GradMeta))) +
-                 (size_t)warp * stages * ld;
-  if (lane == 0) {
-    for (int q = 0; q < stages; ++q) mbar_init(smem_u32(bars + q), 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
-  const double tr_out = (double)(d - 1) / (double)d;
-  const int64_t nbeg = wpart[gw], nend = wpart[gw + 1];
-  const int64_t kb = off[nbeg], ke = off[nend];
-
-  int2 c_eo, n_eo;
-  double c_t, n_t;
-  auto fetch = [&](int64_t base, int2& eo, double& t) {
-    const int64_t k = base + lane;
-    eo = make_int2(0, 0);
-    t = -1.0;  // inert
-    if (k < ke) {
-      eo = inc[k];
-      const uint8_t kd = kind[eo.x];
-      t = kd == K_IN ? 1.0 : (kd == K_OUT ? (double)alpha[eo.x] * tr_out : -1.0);
-    }
-  };
-  fetch(kb, c_eo, c_t);
-  fetch(kb + 32, n_eo, n_t);
-  int64_t c_base = kb, pk = kb;
-  int pslot = 0;
-  auto issue = [&]() {
-    if (pk >= ke) return;
-    if (pk - c_base >= 32) {
-      c_eo = n_eo;
-      c_t = n_t;
-      c_base += 32;
-      fetch(c_base + 32, n_eo, n_t);
-    }
-    const int src = (int)(pk - c_base);
-    const int ex = __shfl_sync(0xffffffffu, c_eo.x, src);
-    const int ey = __shfl_sync(0xffffffffu, c_eo.y, src);
-    const double t = __shfl_sync(0xffffffffu, c_t, src);
-    if (lane == 0) {
-      GradMeta gm;
-      gm.t = t < 0.0 ? 0.0 : t;
-      gm.other = ey;
-      gm.live = t < 0.0 ? 0 : 1;
-      smeta[pslot] = gm;
-      const uint32_t bar = smem_u32(bars + pslot);
-      if (!gm.live) {
-        mbar_arrive(bar);
-      } else {
-        mbar_arrive_tx(bar, rowb);
-        bulk_g2s(smem_u32(ring + (size_t)pslot * ld), Ut + (int64_t)ex * ld, rowb, bar);
-      }
-    }
-    ++pk;
-    if (++pslot == stages) pslot = 0;
-  };
-  for (int q = 0; q < stages; ++q) issue();
-  __syncwarp();
-
-  int cslot = 0;
-  uint32_t cpar = 0;
-  int64_t ck = kb;
-  bool ok = true;
-  double acc[2] = {0.0, 0.0};
-  for (int64_t i = nbeg; i < nend; ++i) {
-    const int64_t eend = off[i + 1];
-    double g[CH][4], a4[CH][4];
-    row_load<LANES, CH>(X + i * ld, ld, lane, g);
-    row_load<LANES, CH>(Ap + i * ld, ld, lane, a4);
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        g[c][k] -= a4[c][k];
-        acc[1] += 0.5 * g[c][k] * g[c][k];
-      }
-    double diag = 0.0;
-    for (; ck < eend && ok; ++ck) {
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(bars + cslot), cpar))) {
-        ok = false;
-        if (lane == 0) atomicOr(&ctl->fault, 1u);
-        break;
-      }
-      const GradMeta gm = smeta[cslot];
-      if (gm.live) {
-        const double* ur = ring + (size_t)cslot * ld;
-        const double sg = (i < gm.other) ? 1.0 : -1.0;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int q = c * LANES + lane;
-          if (4 * q < ld) {
-            double u4[4];
-            Vec4<double>::load(ur + 4 * q, u4);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) g[c][k] += sg * u4[k];
-          }
-        }
-        diag += gm.t;
-      }
-      __syncwarp();
-      if (++cslot == stages) {
-        cslot = 0;
-        cpar ^= 1u;
-      }
-      issue();
-    }
-    if (!ok) break;
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[0] += g[c][k] * g[c][k];
-    row_store<LANES, CH>(G + i * ld, ld, lane, g);
-    if (lane == 0) Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
-  }
-  if (!ok) {
-    for (; ck < pk; ++ck) {
-      mbar_wait(smem_u32(bars + cslot), cpar);
-      if (++cslot == stages) {
-        cslot = 0;
-        cpar ^= 1u;
-      }
-    }
-  }
-  double tot[2];
-  if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_N], tot) && threadIdx.x == 0) {
-    ctl->eval[2] = tot[0];
-    ctl->eval[1] = tot[1];
-  }
-}
-
 // ------------------------------------------------------------ CG
 // Preconditioned CG on V dx = -G in the Chronopoulos-Gear arrangement, which
 // needs one reduction phase per operator application and applies V to
@@ -424,8 +265,8 @@ __device__ __forceinline__ void cg_set_alpha(Ctl* ctl, double delta) {
 // delta = <W, u>. Node-parallel pull over the CSR of B^T: a group of LANES
 // threads owns node i and visits its incidences in increasing edge id,
 // gathering the other endpoint's R row (and yhat_l for outside edges) into
-// registers. Used for short rows; k_cg_matvec_tma stages long rows through
-// shared memory with bulk copies.
+// registers. Used for short rows and the adjoint; k_cg_matvec_ring stages long
+// rows through shared memory.
 template <int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
 k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __restrict__ Dg,
@@ -506,203 +347,6 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
       }
     acc[0] += (double)dot;
     row_store<LANES, CH>(W + i * ld, ld, lane, accv);
-  }
-  double tot[1];
-  if (grid_reduce<1>(acc, partials, &ctl->counter[C_MV], tot) && threadIdx.x == 0)
-    cg_set_alpha(ctl, tot[0]);
-}
-
-// The operator of k_cg_matvec for long rows (one warp per node, LANES = 32).
-// Each warp owns a contiguous node range (balanced by incidences + 2 per node,
-// wpart) and so a contiguous run of CSR incidences. Its lane 0 streams the
-// other endpoint's R row and, for outside edges, the yhat row of every
-// incidence into a per-warp ring of `stages` shared-memory slots with 1-D bulk
-// copies, each slot completing on its own mbarrier; the 32 lanes consume the
-// slots in order and refill each one as soon as they have read it, so `stages`
-// incidences per warp are always in flight and no row is held in registers
-// while it is in flight. Incidence records come in lane-parallel batches of 32,
-// prefetched one batch ahead. Waits are bounded (ctl->fault records a timeout;
-// the warp then drains its own copies, also bounded, and stops computing).
-// Shared memory: header of nw*stages (mbarrier + IncMeta), then
-// nw*stages*2*ld elements of Tc.
-
-template <int CH, typename Tc>
-__global__ void __launch_bounds__(256, 1)
-k_cg_matvec_tma(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __restrict__ Dg,
-                Tc* __restrict__ W, const Tc* __restrict__ Yh,
-                const IncMeta<Tc>* __restrict__ meta, const int64_t* __restrict__ off,
-                const int2* __restrict__ inc, const int* __restrict__ wpart, double sigma,
-                int64_t n, int ld, int stages, double* partials, Ctl* ctl) {
-  constexpr int LANES = 32;
-  extern __shared__ __align__(128) unsigned char smem[];
-  if (!ctl->cg.active) return;
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * nw + warp;
-  const uint32_t rowb = (uint32_t)ld * (uint32_t)sizeof(Tc);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * stages;
-  IncMeta<Tc>* smeta = reinterpret_cast<IncMeta<Tc>*>(smem + (size_t)nw * stages * 8) +
-                       (size_t)warp * stages;
-  Tc* ring = reinterpret_cast<Tc*>(smem + tma_ring_header(nw, stages, sizeof(IncMeta<Tc>))) +
-             (size_t)warp * stages * 2 * ld;
-  if (lane == 0) {
-    for (int q = 0; q < stages; ++q) mbar_init(smem_u32(bars + q), 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
-
-  const int64_t nbeg = wpart[gw], nend = wpart[gw + 1];
-  const int64_t kb = off[nbeg], ke = off[nend];
-
-  // ---- producer state (warp-uniform; lane 0 issues)
-  int2 c_eo, n_eo;
-  IncMeta<Tc> c_m, n_m;
-  auto fetch = [&](int64_t base, int2& eo, IncMeta<Tc>& mm) {
-    const int64_t k = base + lane;
-    if (k < ke) {
-      eo = inc[k];
-      mm = meta[k];
-    } else {
-      eo = make_int2(0, 0);
-      mm.c = (Tc)0;
-      mm.mo = (Tc)0;
-    }
-  };
-  fetch(kb, c_eo, c_m);
-  fetch(kb + 32, n_eo, n_m);
-  int64_t c_base = kb, pk = kb;
-  int pslot = 0;
-  // R rows are gathered by every neighbour: keep them in L2; yhat rows stream
-  const uint64_t pol_keep = l2_policy_evict_last(), pol_stream = l2_policy_evict_first();
-  auto issue = [&]() {
-    if (pk >= ke) return;
-    if (pk - c_base >= 32) {
-      c_eo = n_eo;
-      c_m = n_m;
-      c_base += 32;
-      fetch(c_base + 32, n_eo, n_m);
-    }
-    const int src = (int)(pk - c_base);
-    const int ex = __shfl_sync(0xffffffffu, c_eo.x, src);
-    const int ey = __shfl_sync(0xffffffffu, c_eo.y, src);
-    const Tc mc = __shfl_sync(0xffffffffu, c_m.c, src);
-    const Tc mo = __shfl_sync(0xffffffffu, c_m.mo, src);
-    if (lane == 0) {
-      smeta[pslot].c = mc;
-      smeta[pslot].mo = mo;
-      const uint32_t bar = smem_u32(bars + pslot);
-      if (mc == (Tc)0) {
-        mbar_arrive(bar);
-      } else {
-        Tc* dst = ring + (size_t)pslot * 2 * ld;
-        const bool out = mc < (Tc)0;
-        mbar_arrive_tx(bar, out ? 2u * rowb : rowb);
-        bulk_g2s_hint(smem_u32(dst), R + (int64_t)ey * ld, rowb, bar, pol_keep);
-        if (out) bulk_g2s_hint(smem_u32(dst + ld), Yh + (int64_t)ex * ld, rowb, bar, pol_stream);
-      }
-    }
-    ++pk;
-    if (++pslot == stages) pslot = 0;
-  };
-  for (int q = 0; q < stages; ++q) issue();
-  __syncwarp();  // lane 0's slot metadata before any lane reads it
-
-  // ---- consumer
-  const Tc sg = (Tc)sigma;
-  int cslot = 0;
-  uint32_t cpar = 0;
-  int64_t ck = kb;
-  bool ok = true;
-  double acc[1] = {0.0};
-  for (int64_t i = nbeg; i < nend; ++i) {
-    const int64_t eend = off[i + 1];
-    Tc u[CH][4], accv[CH][4];
-    const Tc mi = Minv[i];
-    row_load<LANES, CH>(R + i * ld, ld, lane, u);
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        u[c][k] *= mi;
-        accv[c][k] = (Tc)0;
-      }
-    for (; ck < eend && ok; ++ck) {
-      // the warp agrees on the outcome (a lane that gave up stops all of them)
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(bars + cslot), cpar))) {
-        ok = false;
-        if (lane == 0) atomicOr(&ctl->fault, 1u);
-        break;
-      }
-      const IncMeta<Tc> mm = smeta[cslot];
-      if (mm.c != (Tc)0) {
-        const Tc* rr = ring + (size_t)cslot * 2 * ld;
-        Tc v[CH][4];
-        row_load<LANES, CH>(rr, ld, lane, v);
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) v[c][k] = u[c][k] - mm.mo * v[c][k];
-        if (mm.c < (Tc)0) {
-          // yhat is read twice from shared memory rather than held in registers
-          const Tc* yy = rr + ld;
-          Tc s = (Tc)0;
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int q = c * LANES + lane;
-            if (4 * q < ld) {
-              Tc y4[4];
-              Vec4<Tc>::load(yy + 4 * q, y4);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) s += y4[k] * v[c][k];
-            }
-          }
-          s = group_sum<LANES>(s, 0xffffffffu);
-          const Tc a = -mm.c;
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int q = c * LANES + lane;
-            if (4 * q < ld) {
-              Tc y4[4];
-              Vec4<Tc>::load(yy + 4 * q, y4);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) accv[c][k] += a * (v[c][k] - s * y4[k]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < CH; ++c)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) accv[c][k] += v[c][k];
-        }
-      }
-      __syncwarp();
-      if (++cslot == stages) {
-        cslot = 0;
-        cpar ^= 1u;
-      }
-      issue();  // refill the slot just read
-    }
-    if (!ok) break;
-    Tc dot = (Tc)0;
-    const Tc di = Dg ? Dg[i] : (Tc)1;
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        accv[c][k] = di * u[c][k] + sg * accv[c][k];
-        dot += u[c][k] * accv[c][k];
-      }
-    acc[0] += (double)dot;
-    row_store<LANES, CH>(W + i * ld, ld, lane, accv);
-  }
-  if (!ok) {
-    // drain this warp's copies still in flight (bounded) before the CTA exits
-    for (; ck < pk; ++ck) {
-      mbar_wait(smem_u32(bars + cslot), cpar);
-      if (++cslot == stages) {
-        cslot = 0;
-        cpar ^= 1u;
-      }
-    }
   }
   double tot[1];
   if (grid_reduce<1>(acc, partials, &ctl->counter[C_MV], tot) && threadIdx.x == 0)
@@ -949,103 +593,18 @@ __global__ void k_unpad_rows(const double* __restrict__ src, double* __restrict_
 
 static constexpr int kMaxPartBlocksPerSm = 8;  // partial-sum slots per SM
 
-// Launch shape of the bulk-copy operator: nw warps per CTA, one CTA per SM
-// (its shared memory fills most of one SM), `stages` ring slots per warp.
-struct TmaShape {
-  int nw = 0, stages = 0;
-  size_t smem = 0;
-};
-template <typename Tc>
-inline TmaShape tma_shape(int ld) {
-  constexpr size_t kBudget = 200 * 1024;
-  TmaShape sh;
-  const size_t slot = 2 * (size_t)ld * sizeof(Tc);
-  for (int nw : {8, 4}) {
-    int st = (int)std::min<size_t>(8, kBudget / ((size_t)nw * slot));
-    if (st >= 2) {
-      sh.nw = nw;
-      sh.stages = st;
-      sh.smem = tma_ring_header(nw, st, sizeof(IncMeta<Tc>)) + (size_t)nw * st * slot;
-      return sh;
-    }
-  }
-  return sh;
-}
-
-// Shape of the bulk-copy node gradient with the operator's warps per CTA (so
-// both share one node partition): float64 Ut rows, one per slot.
-inline TmaShape grad_shape(const TmaShape& op, int ld) {
-  constexpr size_t kBudget = 200 * 1024;
-  TmaShape sh;
-  if (op.nw <= 0) return sh;
-  const size_t slot = (size_t)ld * 8;
-  const int st = (int)std::min<size_t>(8, kBudget / ((size_t)op.nw * slot));
-  if (st < 2) return sh;
-  sh.nw = op.nw;
-  sh.stages = st;
-  sh.smem = tma_ring_header(op.nw, st, sizeof(GradMeta)) + (size_t)op.nw * st * slot;
-  return sh;
-}
-
-// Node-gradient launch: the bulk-copy form when `wpart` and a shape are given.
+// Register-form operator launch (grid sized to the node groups, at most 4 blocks per SM).
 template <int L, int CH, typename Tc>
-inline int launch_node_grad(Ctx* c, const double* X, const double* Ap, const double* Ut,
-                            const int64_t* off, const int2* inc, const Tc* alpha,
-                            const uint8_t* kind, double sigma, int d, double* G, Tc* Minv,
-                            const int* wpart, const TmaShape& sh, int64_t n, int ld,
-                            double* part, Ctl* ctl, cudaStream_t s) {
-  if (L == 32 && wpart && sh.nw > 0) {
-    static size_t attr_set[64] = {};
-    size_t& cur = attr_set[c->device & 63];
-    if (cur < sh.smem) {
-      CCM_CUDA(cudaFuncSetAttribute(k_node_grad_tma<CH, Tc>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
-      cur = sh.smem;
-    }
-    k_node_grad_tma<CH, Tc><<<c->num_sms, sh.nw * 32, sh.smem, s>>>(
-        X, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv, wpart, n, ld, sh.stages, part, ctl);
-  } else {
-    const int threads = 256;
-    const int gpb = threads / L;
-    const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
-    k_node_grad<L, CH, Tc><<<blocks, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma, d,
-                                                      G, Minv, n, ld, part, ctl);
-  }
-  CCM_COUNT(c);
-  return CCM_OK;
-}
-
-// Node ranges of the nwg warps of the bulk-copy operator, balanced by
-// (incidences + 2 per node): part[w] = first node with off[i] + 2i >= w * total / nwg.
-__global__ void k_warp_partition(const int64_t* __restrict__ off, int64_t n, int nwg,
-                                 int* __restrict__ part);
-
-// Operator launch: the bulk-copy form for rows of at least 32 quads (LANES = 32)
-// when `wpart` is given, the register form otherwise.
-template <int L, int CH, typename Tc>
-inline int launch_matvec(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, Tc* W, const Tc* Yh,
-                         const IncMeta<Tc>* meta, const int64_t* off, const int2* inc,
-                         const int* wpart, const TmaShape& sh, double sigma, int64_t n, int ld,
-                         double* part, Ctl* ctl, cudaStream_t s) {
-  if (L == 32 && wpart && sh.nw > 0) {
-    static size_t attr_set[64] = {};  // largest dynamic shared memory enabled, per device
-    size_t& cur = attr_set[c->device & 63];
-    if (cur < sh.smem) {
-      CCM_CUDA(cudaFuncSetAttribute(k_cg_matvec_tma<CH, Tc>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
-      cur = sh.smem;
-    }
-    k_cg_matvec_tma<CH, Tc><<<c->num_sms, sh.nw * 32, sh.smem, s>>>(
-        R, Minv, Dg, W, Yh, meta, off, inc, wpart, sigma, n, ld, sh.stages, part, ctl);
-  } else {
-    const int threads = 256;
-    const int gpb = threads / L;
-    const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
-    k_cg_matvec<L, CH, Tc><<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma,
-                                                      n, ld, part, ctl);
-  }
+inline int launch_matvec_reg(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, Tc* W,
+                             const Tc* Yh, const IncMeta<Tc>* meta, const int64_t* off,
+                             const int2* inc, double sigma, int64_t n, int ld, double* part,
+                             Ctl* ctl, cudaStream_t s) {
+  const int threads = 256;
+  const int gpb = threads / L;
+  const int blocks =
+      (int)std::max<int64_t>(1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
+  k_cg_matvec<L, CH, Tc><<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma, n,
+                                                    ld, part, ctl);
   CCM_COUNT(c);
   return CCM_OK;
 }

@@ -327,8 +327,8 @@ static int run_vjp(Ctx* c, const double* A, int64_t n, int d, const int2* edges,
     const int CHUNK = 16;
     for (int chunk = 0; chunk * CHUNK < maxit; ++chunk) {
       for (int k = 0; k < CHUNK; ++k) {
-        CCM_TRY(launch_matvec<L, CH, double>(c, R, Minv, Dg, Qv, S, meta, coff, cinc, nullptr,
-                                             TmaShape{}, 1.0, K, ld, part, ctl, s));
+        CCM_TRY(launch_matvec_reg<L, CH, double>(c, R, Minv, Dg, Qv, S, meta, coff, cinc, 1.0,
+                                                 K, ld, part, ctl, s));
         k_cg_update<double><<<b_quad, threads, 0, s>>>(lam, Pa, Pb, R, Qv, Minv, K, ld, part,
                                                        ctl);
         CCM_COUNT(c);

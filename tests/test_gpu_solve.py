@@ -125,3 +125,33 @@ def test_labels_entry_point(ccm):
                         torch.tensor(E, dtype=torch.int32, device="cuda:0"))
     assert lab.cpu().tolist() == olabels.labels(X, E).tolist() == [0, 0, 1, 2, 2]
     assert K == 3
+
+
+def _hub_graph(seed, n, d, k):
+    """kNN graph plus one hub joined to every other node, one isolated node and
+    some inert edges: long rows (d > 128) run the shared-memory ring kernels,
+    whose even split of the incidence stream cuts the hub into many parts."""
+    rng = np.random.default_rng(seed)
+    cent = rng.normal(0, 2, size=(4, d))
+    A = cent[rng.integers(0, 4, n)] + rng.normal(size=(n, d))
+    edges, w, _ = ograph.build_graph(A[: n - 1], k, 0.0)   # node n-1 stays isolated
+    hub = 3
+    extra = np.array([[min(hub, j), max(hub, j)] for j in range(n - 1) if j != hub])
+    allE = np.concatenate([edges, extra])
+    allw = np.concatenate([w, np.full(len(extra), 0.02)])
+    key = allE[:, 0] * n + allE[:, 1]
+    _, idx = np.unique(key, return_index=True)
+    E, wE = allE[idx], allw[idx]
+    wE[::11] = 0.0                                          # inert edges
+    return A, E, wE
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_long_rows_hub_matches_oracle(ccm, precision):
+    A, E, w = _hub_graph(11, 90, 260, 4)
+    gammas = np.array([0.5, 5.0, 20.0, 80.0])         # 90, 90, 6, 5 clusters
+    X, _ = _check_path(ccm, A, E, w, gammas, precision, engine=1)
+    At, Et, wt = _to_dev(A, E, w)
+    X1, L1, _, _ = ccm.solve_path(At, Et, wt, gammas, tol=SOLVE_TOL, precision=precision, engine=1)
+    X2, L2, _, _ = ccm.solve_path(At, Et, wt, gammas, tol=SOLVE_TOL, precision=precision, engine=1)
+    assert torch.equal(X1, X2) and torch.equal(L1, L2)     # split parts sum in a fixed order
