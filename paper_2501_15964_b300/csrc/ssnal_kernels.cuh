@@ -88,12 +88,15 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
       kind[e] = kd;
       alpha[e] = (Tc)a;
     }
-    double o[CH][4];
+    if (kd == K_IN) {
+      row_store<LANES, CH>(Ut + e * ld, ld, lane, y);  // Pi(y) = y inside the ball
+    } else {
 #pragma unroll
-    for (int c = 0; c < CH; ++c)
+      for (int c = 0; c < CH; ++c)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) o[c][k] = scale * y[c][k];
-    row_store<LANES, CH>(Ut + e * ld, ld, lane, o);
+        for (int k = 0; k < 4; ++k) xi[c][k] = scale * y[c][k];
+      row_store<LANES, CH>(Ut + e * ld, ld, lane, xi);
+    }
     if (kd == K_OUT) {
       // yhat in the operator's precision: for float32 the scaling runs in
       // float32 (FP64 throughput is the limit of this kernel)
@@ -435,65 +438,11 @@ k_trial(const double* __restrict__ X, const Tc* __restrict__ Dx, const double* _
 }
 
 // ------------------------------------------------------------ KKT / objectives
-// Per edge: BX_l, prox residual ||BX - prox_p(BX + U)||^2 and r_l ||BX_l||.
-template <int LANES, int CH>
-__global__ void __launch_bounds__(256)
-k_kkt_edge(const double* __restrict__ X, const double* __restrict__ U,
-           const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
-           int64_t m, int ld, double* partials, Ctl* ctl) {
-  const int lane = threadIdx.x % LANES;
-  const unsigned mask = group_mask<LANES>();
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
-  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
-  double acc[2] = {0.0, 0.0};
-  for (int64_t e = g0; e < m; e += ng) {
-    int2 ij = edges[e];
-    double r = gamma * w[e];
-    double bx[CH][4], v[CH][4];
-    row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, bx);
-    row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, v);
-    double sb = 0.0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bx[c][k] -= v[c][k];
-        sb += bx[c][k] * bx[c][k];
-      }
-    row_load<LANES, CH>(U + e * ld, ld, lane, v);
-    double sv = 0.0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        v[c][k] += bx[c][k];
-        sv += v[c][k] * v[c][k];
-      }
-    sb = group_sum<LANES>(sb, mask);
-    sv = group_sum<LANES>(sv, mask);
-    double nv = sqrt(sv);
-    double shrink = (nv > r) ? 1.0 - r / nv : 0.0;
-    double sres = 0.0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        double res = bx[c][k] - shrink * v[c][k];
-        sres += res * res;
-      }
-    acc[0] += sres;
-    if (lane == 0) acc[1] += r * sqrt(sb);
-  }
-  double tot[2];
-  if (grid_reduce<2>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {
-    ctl->kkt[0] = tot[0];
-    ctl->kkt[1] = tot[1];
-  }
-}
-
 // KKT edge pass fused with the next evaluation at the same (X, U): per edge
-// bx = x_i - x_j feeds both the prox residual / r||bx|| (as k_kkt_edge) and
-// y = u + sigma bx with its kind, alpha, yhat, Pi(y) and h (as k_edge_eval).
+// bx = x_i - x_j feeds both the primal residual ||BX - prox_p(BX + U)||^2 and
+// r_l ||bx|| (for f_p) and y = u + sigma bx with its kind, alpha, yhat, Pi(y)
+// and h (as k_edge_eval). With v = u + bx and shrink = max(0, 1 - r/||v||),
+// BX - prox_p(BX + U) = bx - shrink v.
 template <int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
 k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
@@ -520,10 +469,10 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
       for (int k = 0; k < 4; ++k) {
         bx[c][k] -= y[c][k];
         sb = fma(bx[c][k], bx[c][k], sb);
-        const double v = u[c][k] + bx[c][k];
-        sv = fma(v, v, sv);
         y[c][k] = fma(sigma, bx[c][k], u[c][k]);
         ss = fma(y[c][k], y[c][k], ss);
+        u[c][k] += bx[c][k];  // u now holds v = u + bx
+        sv = fma(u[c][k], u[c][k], sv);
       }
     sb = group_sum<LANES>(sb, mask);
     sv = group_sum<LANES>(sv, mask);
@@ -535,7 +484,7 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
     for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const double res = bx[c][k] - shrink * (u[c][k] + bx[c][k]);
+        const double res = fma(-shrink, u[c][k], bx[c][k]);
         sres = fma(res, res, sres);
       }
     acc[0] += sres;
@@ -556,11 +505,15 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
       kind[e] = kd;
       alpha[e] = (Tc)a;
     }
+    if (kd == K_IN) {
+      row_store<LANES, CH>(Ut + e * ld, ld, lane, y);  // Pi(y) = y inside the ball
+    } else {
 #pragma unroll
-    for (int c = 0; c < CH; ++c)
+      for (int c = 0; c < CH; ++c)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) u[c][k] = scale * y[c][k];
-    row_store<LANES, CH>(Ut + e * ld, ld, lane, u);
+        for (int k = 0; k < 4; ++k) u[c][k] = scale * y[c][k];
+      row_store<LANES, CH>(Ut + e * ld, ld, lane, u);
+    }
     if (kd == K_OUT) {
       const Tc invc = (Tc)(1.0 / ny);
       Tc yh[CH][4];
