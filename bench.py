@@ -165,6 +165,21 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def job_rate(ms_local, units_per_rank, dist=None, device="cpu"):
+    """Whole-job throughput of a replicated run: every rank processed
+    `units_per_rank` units in its own `ms_local` milliseconds; the job took the
+    slowest rank's time (MAX over ranks). Returns (units per second, job ms)."""
+    import torch
+    ms = float(ms_local)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        world = dist.get_world_size()
+    return world * units_per_rank / (ms / 1000.0), ms
+
+
 def _time(fn, stream, reps=1):
     import torch
     torch.cuda.synchronize()
@@ -259,6 +274,8 @@ def main():
                     help="synthetic workload (default: the MNIST-shaped one)")
     ap.add_argument("--n-gamma", type=int, default=0,
                     help="solve only the first N gammas of the path (profiling runs)")
+    ap.add_argument("--gamma-from", type=int, default=0,
+                    help="start the path at this index of the gamma grid, cold (profiling runs)")
     ap.add_argument("--form", default="path", choices=["path", "batched", "adjoint"],
                     help="path (default, the JSON contract line), batched or adjoint comparison")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched form")
@@ -293,6 +310,7 @@ def main():
 
     prec = 1 if args.precision == "mixed" else 0
     A, wl, gam = make_problem(rank)
+    gam = gam[args.gamma_from:]
     if args.n_gamma > 0:
         gam = gam[: args.n_gamma]
     T = len(gam)
@@ -330,12 +348,7 @@ def main():
         ev1.record(stream)
         barrier()
     launches = ccm.launch_count() - l0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * T * args.steps / (ms / 1000.0)
+    value, ms = job_rate(ev0.elapsed_time(ev1), T * args.steps, dist, dev)
 
     # end-to-end: pinned host A -> device, full path, X and labels back to pinned host
     X_host = torch.empty((T, A.shape[0], A.shape[1]), dtype=torch.float64).pin_memory()
@@ -351,12 +364,7 @@ def main():
         L_host.copy_(lab, non_blocking=True)
     e1.record(stream)
     barrier()
-    ems = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ems], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
-    e2e = world * T * args.steps / (ems / 1000.0)
+    e2e, ems = job_rate(e0.elapsed_time(e1), T * args.steps, dist, dev)
 
     if rank == 0:
         peak, peak_kind = _peaks()

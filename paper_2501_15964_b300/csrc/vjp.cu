@@ -10,7 +10,8 @@
 //     dL/da_i = lambda_c(i),   dL/dw_l = -gamma s_l^T (lambda_c(i) - lambda_c(j)) (l in N), 0 else.
 // H is the Newton-CG operator of the solver applied on the cluster graph with
 // alpha_l = c_l, yhat_l = s_l, sigma = 1 and the diagonal M instead of I, so the
-// same node-pull kernel (k_cg_matvec) and CG kernels run it, in float64.
+// same node-pull kernel (k_cg_matvec) and CG kernels solve it: float32 CG on the
+// corrections of a float64 iterative refinement (residuals in float64).
 //
 // Cluster member lists and the cluster-level incidence lists are built with a
 // bitonic sort of (cluster, index) keys, so every sum has a fixed order and the
@@ -214,6 +215,78 @@ __global__ void k_vjp_scatter_w(const double* __restrict__ lam, const int32_t* _
   }
 }
 
+// rneg = bneg + H lambda, the negated residual of H lambda = -bneg (float64),
+// and ||rneg||^2 -> ctl->dots[0]. H = M (x) I + sum_{l in N} c_l B_l^T (I - s_l s_l^T) B_l
+// on the cluster graph: the operator of k_cg_matvec applied to lambda itself.
+template <int L, int CH>
+__global__ void __launch_bounds__(256)
+k_vjp_residual(const double* __restrict__ lam, const double* __restrict__ bneg,
+               const double* __restrict__ Dg, const double* __restrict__ S,
+               const double* __restrict__ coef, const int64_t* __restrict__ coff,
+               const int2* __restrict__ cinc, int64_t K, int ld, double* __restrict__ rneg,
+               double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % L;
+  const unsigned mask = group_mask<L>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / L;
+  double acc1[1] = {0.0};
+  for (int64_t i = g0; i < K; i += ng) {
+    double li[CH][4], h[CH][4];
+    row_load<L, CH>(lam + i * ld, ld, lane, li);
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) h[c][k] = 0.0;
+    for (int64_t t = coff[i]; t < coff[i + 1]; ++t) {
+      const int2 eo = cinc[t];
+      double v[CH][4], sl[CH][4];
+      row_load<L, CH>(lam + (int64_t)eo.y * ld, ld, lane, v);
+      row_load<L, CH>(S + (int64_t)eo.x * ld, ld, lane, sl);
+      double dot = 0.0;
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          v[c][k] = li[c][k] - v[c][k];
+          dot += sl[c][k] * v[c][k];
+        }
+      dot = group_sum<L>(dot, mask);
+      const double a = coef[eo.x];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[c][k] += a * (v[c][k] - dot * sl[c][k]);
+    }
+    double b4[CH][4];
+    row_load<L, CH>(bneg + i * ld, ld, lane, b4);
+    const double di = Dg[i];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        h[c][k] = b4[c][k] + (di * li[c][k] + h[c][k]);
+        acc1[0] += h[c][k] * h[c][k];
+      }
+    row_store<L, CH>(rneg + i * ld, ld, lane, h);
+  }
+  double tot[1];
+  if (grid_reduce<1>(acc1, partials, &ctl->counter[C_TRIAL], tot) && threadIdx.x == 0)
+    ctl->dots[0] = tot[0];
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t count) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x)
+    b[q] = (float)a[q];
+}
+
+// lambda += delta (float correction into the float64 iterate)
+__global__ void k_add_f2d(double* __restrict__ lam, const float* __restrict__ dlt, int64_t count) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x)
+    lam[q] += (double)dlt[q];
+}
+
 // ---------------------------------------------------------------- host engine
 template <int L, int CH>
 static int run_vjp(Ctx* c, const double* A, int64_t n, int d, const int2* edges, const double* w,
@@ -251,21 +324,23 @@ static int run_vjp(Ctx* c, const double* A, int64_t n, int d, const int2* edges,
   double* bneg = (double*)p;
   CCM_TRY(ws_get(c, S_DX, (size_t)n * ld * 8, &p));
   double* lam = (double*)p;
-  CCM_TRY(ws_get(c, S_R, (size_t)n * ld * 8, &p));
-  double* R = (double*)p;
-  CCM_TRY(ws_get(c, S_X0, (size_t)n * ld * 8, &p));
-  double* Pa = (double*)p;
-  CCM_TRY(ws_get(c, S_X1, (size_t)n * ld * 8, &p));
-  double* Pb = (double*)p;
   CCM_TRY(ws_get(c, S_G, (size_t)n * ld * 8, &p));
-  double* Qv = (double*)p;
+  double* Qv = (double*)p;  // negated residual of the float64 system
   CCM_TRY(ws_get(c, S_U, (size_t)n * 8 * 2, &p));
   double* Dg = (double*)p;
   double* Minv = Dg + n;
   CCM_TRY(ws_get(c, S_PART, (size_t)kMaxPartBlocksPerSm * c->num_sms * 4 * 8, &p));
   double* part = (double*)p;
-  CCM_TRY(ws_get(c, S_META, (size_t)std::max<int64_t>(2 * m2, 1) * sizeof(IncMeta<double>), &p));
-  IncMeta<double>* meta = (IncMeta<double>*)p;
+  // float32 copies for the correction solves: 5 vectors of n x ld, Minv and D
+  // (n each), yhat rows (m x ld), c_l (m), packed incidence coefficients (2 m2)
+  const size_t f_vec = (size_t)round_up((int64_t)5 * n * ld + 2 * n, 64) * 4;
+  const size_t f_sy = (size_t)round_up(std::max<int64_t>(m, 1) * ld, 64) * 4;
+  const size_t f_cf = (size_t)round_up(std::max<int64_t>(m, 1), 64) * 4;
+  CCM_TRY(ws_get(c, S_VJPF, f_vec + f_sy + f_cf + (size_t)2 * m2 * sizeof(IncMeta<float>), &p));
+  float* vf = (float*)p;
+  float* Syf = (float*)((char*)p + f_vec);
+  float* coeff = (float*)((char*)p + f_vec + f_sy);
+  IncMeta<float>* metaf = (IncMeta<float>*)((char*)p + f_vec + f_sy + f_cf);
   CCM_TRY(ws_get(c, S_CTRL, sizeof(Ctl), &p));
   Ctl* ctl = (Ctl*)p;
   void* hp;
@@ -315,28 +390,60 @@ static int run_vjp(Ctx* c, const double* A, int64_t n, int d, const int2* edges,
                                         Minv);
     CCM_COUNT(c);
     CCM_CUDA(cudaGetLastError());
-    // CG on H lambda = Q^T G (K rows of ld), float64
+    // H lambda = Q^T G by mixed-precision iterative refinement: the residual
+    // r = Q^T G - H lambda in float64 (k_vjp_residual), the correction H delta = r
+    // by float32 CG with the operator kernels (relative tolerance 1e-3, at most 400
+    // iterations), lambda += delta in float64; stop at ||r|| <= 1e-11 ||Q^T G||, when a
+    // correction no longer halves ||r||, or after 16 corrections.
     const int b_node = (int)std::max<int64_t>(1, std::min<int64_t>((K + gpb - 1) / gpb, maxb));
     const int b_elem = nb((int64_t)K * ld);
     const int b_quad = nb(((int64_t)K * ld + 3) / 4);
-    const int maxit = 5000;
-    k_cg_init<double><<<b_elem, threads, 0, s>>>(bneg, Minv, R, lam, K, ld, 1e-11, maxit, cinc,
-                                                 kind, coef, meta, nvalid, part, ctl);
-    CCM_COUNT(c);
-    CCM_CUDA(cudaGetLastError());
-    const int CHUNK = 16;
-    for (int chunk = 0; chunk * CHUNK < maxit; ++chunk) {
-      for (int k = 0; k < CHUNK; ++k) {
-        CCM_TRY(launch_matvec_reg<L, CH, double>(c, R, Minv, Dg, Qv, S, meta, coff, cinc, 1.0,
-                                                 K, ld, part, ctl, s));
-        k_cg_update<double><<<b_quad, threads, 0, s>>>(lam, Pa, Pb, R, Qv, Minv, K, ld, part,
-                                                       ctl);
-        CCM_COUNT(c);
-      }
+    const int64_t kl = (int64_t)K * ld;
+    float* Rf = vf;
+    float* Pf = Rf + kl;
+    float* Sf = Pf + kl;
+    float* Wf = Sf + kl;
+    float* Df = Wf + kl;
+    float* Minvf = Df + kl;
+    float* Dgf = Minvf + K;
+    k_d2f<<<nb(m * ld), threads, 0, s>>>(S, Syf, m * ld);
+    k_d2f<<<nb(m), threads, 0, s>>>(coef, coeff, m);
+    k_d2f<<<nb(K), threads, 0, s>>>(Minv, Minvf, K);
+    k_d2f<<<nb(K), threads, 0, s>>>(Dg, Dgf, K);
+    CCM_COUNT(c); CCM_COUNT(c); CCM_COUNT(c); CCM_COUNT(c);
+    CCM_CUDA(cudaMemsetAsync(lam, 0, (size_t)kl * 8, s));
+    double r2_0 = -1.0, r2_prev = 0.0;
+    for (int ref = 0; ref <= 16; ++ref) {
+      k_vjp_residual<L, CH><<<b_node, threads, 0, s>>>(lam, bneg, Dg, S, coef, coff, cinc, K, ld,
+                                                       Qv, part, ctl);
+      CCM_COUNT(c);
       CCM_CUDA(cudaGetLastError());
       CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
       CCM_CUDA(cudaStreamSynchronize(s));
-      if (!hc->cg.active) break;
+      const double r2 = hc->dots[0];
+      if (r2_0 < 0.0) r2_0 = r2;
+      if (!(r2 > 1e-22 * r2_0) || ref == 16 || (ref > 0 && !(r2 < 0.25 * r2_prev))) break;
+      r2_prev = r2;
+      k_cg_init<float><<<b_elem, threads, 0, s>>>(Qv, Minvf, Rf, Df, K, ld, 1e-3, 400, cinc,
+                                                  kind, coeff, metaf, nvalid, part, ctl);
+      CCM_COUNT(c);
+      CCM_CUDA(cudaGetLastError());
+      const int CHUNK = 16;
+      for (int chunk = 0; chunk * CHUNK < 400; ++chunk) {
+        for (int k = 0; k < CHUNK; ++k) {
+          CCM_TRY(launch_matvec_reg<L, CH, float>(c, Rf, Minvf, Dgf, Wf, Syf, metaf, coff, cinc,
+                                                  1.0, K, ld, part, ctl, s));
+          k_cg_update<float><<<b_quad, threads, 0, s>>>(Df, Pf, Sf, Rf, Wf, Minvf, K, ld, part,
+                                                        ctl);
+          CCM_COUNT(c);
+        }
+        CCM_CUDA(cudaGetLastError());
+        CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CCM_CUDA(cudaStreamSynchronize(s));
+        if (!hc->cg.active) break;
+      }
+      k_add_f2d<<<b_elem, threads, 0, s>>>(lam, Df, kl);
+      CCM_COUNT(c);
     }
     k_vjp_scatter_a<<<nb(n * d), threads, 0, s>>>(lam, lab, n, d, ld, dLdA, t == 0);
     CCM_COUNT(c);
