@@ -407,10 +407,11 @@ k_node_grad_ring(const double* __restrict__ X, const double* __restrict__ Ap,
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           xa[c][k] -= a4[c][k];
-          hxa += 0.5 * xa[c][k] * xa[c][k];
+          hxa = fma(xa[c][k], xa[c][k], hxa);
           g[c][k] += xa[c][k];
-          gg += g[c][k] * g[c][k];
+          gg = fma(g[c][k], g[c][k], gg);
         }
+      hxa *= 0.5;
       row_store<LANES, CH>(G + (int64_t)i * ld, ld, lane, g);
       if (lane == 0) Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
       if (np > 1) {  // the split node's own reduction row

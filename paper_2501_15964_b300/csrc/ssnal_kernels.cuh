@@ -41,6 +41,27 @@ struct GridShape {
   int blocks, threads;
 };
 
+// float64 -> float32 rounding toward zero from the bit fields (IEEE 754
+// binary64: sign, 11-bit exponent biased by 1023, 52-bit fraction; binary32:
+// 8-bit exponent biased by 127, 23-bit fraction): the high word carries the
+// sign, the exponent and 20 fraction bits, the low word the next 3. Values
+// below 2^-126 in magnitude go to a signed zero; the yhat components this
+// converts are at most 1 in magnitude, so no overflow case arises. Integer
+// operations only: on B300 the FP64 pipe (2 operations per clock per SM) is
+// the limit of the edge passes, and a conversion instruction would occupy it.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned mag = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float((hi & 0x80000000u) | (e > 896u ? mag : 0u));
+}
+template <typename Tc>
+__device__ __forceinline__ Tc to_operator(double x);
+template <>
+__device__ __forceinline__ float to_operator<float>(double x) { return f64_to_f32_rz(x); }
+template <>
+__device__ __forceinline__ double to_operator<double>(double x) { return x; }
+
 // ------------------------------------------------------------ edge evaluation
 // For every edge: y, ||y||, kind, Pi(y) -> Ut, yhat -> Yh (outside edges),
 // alpha; accumulates sum_l h_l(y_l).
@@ -106,7 +127,7 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
 #pragma unroll
       for (int c = 0; c < CH; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)y[c][k] * invc;
+        for (int k = 0; k < 4; ++k) yh[c][k] = to_operator<Tc>(y[c][k]) * invc;
       row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
     }
   }
@@ -368,7 +389,9 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
   const Tc al = (Tc)ctl->cg.alpha;
   const Tc be = (Tc)ctl->cg.beta;
   const bool first = ctl->cg.it == 0;
-  double acc[2] = {0.0, 0.0};
+  // a thread's few quads are summed in Tc, then once in float64 (conversions and
+  // float64 additions occupy B300's narrow FP64 pipe)
+  Tc rz_t = (Tc)0, rr_t = (Tc)0;
   const int64_t total = n * ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; t4 < total;
@@ -404,9 +427,10 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
     Vec4<Tc>::store(P + t4, p);
     Vec4<Tc>::store(S + t4, sv);
     Vec4<Tc>::store(R + t4, r);
-    acc[0] += (double)(mi * rr);
-    acc[1] += (double)rr;
+    rz_t += mi * rr;
+    rr_t += rr;
   }
+  double acc[2] = {(double)rz_t, (double)rr_t};
   double tot[2];
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_UPD], tot) && threadIdx.x == 0) {
     CgCtl& c = ctl->cg;
@@ -520,7 +544,7 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
 #pragma unroll
       for (int c = 0; c < CH; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)y[c][k] * invc;
+        for (int k = 0; k < 4; ++k) yh[c][k] = to_operator<Tc>(y[c][k]) * invc;
       row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
     }
   }
