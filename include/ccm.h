@@ -190,8 +190,10 @@ int ccm_labels_noalloc(const double* X, int64_t n, int32_t d, const int32_t* edg
  * events: clusters are the components of fused edges (rule of ccm_labels);
  * with s_l = (x_i-x_j)/||x_i-x_j|| and c_l = gamma w_l/||x_i-x_j|| on edges
  * joining two clusters, lambda solves (M + sum_l c_l B_l^T (I - s_l s_l^T) B_l) lambda = Q^T G
- * in the cluster space (M = cluster sizes) by conjugate gradients with the
- * Newton-CG operator; dL/da_i = lambda_c(i), dL/dw_l = -gamma s_l^T (lambda_c(i) - lambda_c(j))
+ * in the cluster space (M = cluster sizes) by iterative refinement: float64
+ * residuals, float32 conjugate-gradient corrections with the Newton-CG operator,
+ * until ||residual|| <= 1e-11 ||Q^T G|| (or a correction stops halving it);
+ * dL/da_i = lambda_c(i), dL/dw_l = -gamma s_l^T (lambda_c(i) - lambda_c(j))
  * (0 for fused edges). X: T x n x d from ccm_solve_path. U is accepted for
  * interface symmetry and may be NULL (the gradient depends on X only).
  * gammas: HOST. Both outputs are overwritten (not accumulated into).
