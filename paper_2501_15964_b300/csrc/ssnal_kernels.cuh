@@ -33,13 +33,8 @@ struct Ctl {
   double dots[2];   // <G, Dx>
   double kkt[4];    // ||BX - prox(BX+U)||^2, sum r||BX||, <A, B^T U>, ||B^T U||^2
   unsigned counter[8];
-  unsigned fault;   // nonzero: a bounded device-side wait gave up
 };
 enum CounterId { C_EVAL_E = 0, C_EVAL_N, C_CGI, C_MV, C_UPD, C_TRIAL, C_KKT_E, C_KKT_N };
-
-struct GridShape {
-  int blocks, threads;
-};
 
 // float64 -> float32 rounding toward zero from the bit fields (IEEE 754
 // binary64: sign, 11-bit exponent biased by 1023, 52-bit fraction; binary32:

@@ -155,3 +155,38 @@ def test_long_rows_hub_matches_oracle(ccm, precision):
     X1, L1, _, _ = ccm.solve_path(At, Et, wt, gammas, tol=SOLVE_TOL, precision=precision, engine=1)
     X2, L2, _, _ = ccm.solve_path(At, Et, wt, gammas, tol=SOLVE_TOL, precision=precision, engine=1)
     assert torch.equal(X1, X2) and torch.equal(L1, L2)     # split parts sum in a fixed order
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_long_rows_degenerate_graphs(ccm, precision):
+    """Long rows (ring kernels) on degenerate graphs: no edges (X = A for every
+    gamma), a single node, and one edge between two points (the n = 2 closed
+    form: fused iff 2 gamma w >= ||a_1 - a_2||)."""
+    rng = np.random.default_rng(21)
+    d = 200
+    A = rng.normal(size=(50, d))
+    At = torch.tensor(A, device="cuda:0")
+    E0 = torch.zeros((0, 2), dtype=torch.int32, device="cuda:0")
+    w0 = torch.zeros((0,), dtype=torch.float64, device="cuda:0")
+    X, lab, _, st = ccm.solve_path(At, E0, w0, [0.0, 1.0, 10.0], tol=SOLVE_TOL,
+                                   precision=precision, engine=1)
+    assert torch.equal(X[0], At) and torch.equal(X[2], At)
+    assert lab[2].cpu().tolist() == list(range(50))
+    X1, _, _, _ = ccm.solve_path(At[:1], E0, w0, [0.5], tol=SOLVE_TOL, precision=precision,
+                                 engine=1)
+    assert torch.equal(X1[0], At[:1])
+    a = A[:2]
+    gap = np.linalg.norm(a[0] - a[1])
+    E1 = torch.tensor([[0, 1]], dtype=torch.int32, device="cuda:0")
+    w1 = torch.tensor([1.0], dtype=torch.float64, device="cuda:0")
+    gam = [0.25 * gap, 0.75 * gap]          # below and above the fusion threshold gap / 2
+    # tight tolerance: the fused pair must end below the 1e-6 label threshold
+    X2, lab2, _, _ = ccm.solve_path(At[:2], E1, w1, gam, tol=1e-10, precision=precision,
+                                    engine=1)
+    X2 = X2.cpu().numpy()
+    delta = (a[0] - a[1]) / gap
+    want0 = np.stack([a[0] - gam[0] * delta, a[1] + gam[0] * delta])
+    want1 = np.tile(a.mean(0), (2, 1))
+    assert np.linalg.norm(X2[0] - want0) <= 1e-6 * np.linalg.norm(want0)
+    assert np.linalg.norm(X2[1] - want1) <= 1e-6 * np.linalg.norm(want1)
+    assert lab2.cpu().tolist() == [[0, 1], [0, 0]]
