@@ -262,6 +262,34 @@ def form_vjp(args):
     return 0
 
 
+def form_admm(args):
+    """ADMM (the paper's second solver) against SSNAL on the same GPU, grid
+    engine, same tolerance: the n = 200, d = 2 workload (20 gammas)."""
+    import torch
+    import paper_2501_15964_b300 as ccm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    A, _, wl = synth.make_workload("gmm200_d2", 0)
+    gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    At = torch.tensor(A, device="cuda")
+    E, w, _ = ccm.build_graph(At, wl.k, wl.phi)
+    runs = {}
+    for name, fn in (("ssnal", ccm.solve_path), ("admm", ccm.solve_path_admm)):
+        fn(At, E, w, gam, tol=SOLVE_TOL, engine=1)
+        ms, (_, _, _, st) = _time(lambda: fn(At, E, w, gam, tol=SOLVE_TOL, engine=1), stream,
+                                  args.steps)
+        runs[name] = {"ms": ms, "value": len(gam) / (ms / 1000.0),
+                      "iterations": sum(s["outer"] for s in st), "cg": sum(s["cg"] for s in st),
+                      "max_kkt": max(s["kkt"] for s in st), "max_gap": max(s["gap"] for s in st),
+                      "not_converged": sum(1 for s in st if s["status"] != 0)}
+    line = {"form": "admm", "metric": "gamma-solves/s, ADMM vs SSNAL (grid engine)",
+            "unit": "gamma-solves/s", "workload": "gmm200_d2", "gammas": len(gam),
+            "tol": SOLVE_TOL, "ssnal": runs["ssnal"], "admm": runs["admm"],
+            "ssnal_over_admm": runs["admm"]["ms"] / runs["ssnal"]["ms"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,8 +304,9 @@ def main():
                     help="solve only the first N gammas of the path (profiling runs)")
     ap.add_argument("--gamma-from", type=int, default=0,
                     help="start the path at this index of the gamma grid, cold (profiling runs)")
-    ap.add_argument("--form", default="path", choices=["path", "batched", "adjoint"],
-                    help="path (default, the JSON contract line), batched or adjoint comparison")
+    ap.add_argument("--form", default="path", choices=["path", "batched", "adjoint", "admm"],
+                    help="path (default, the JSON contract line), or the batched, adjoint or "
+                         "ADMM comparison")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched form")
     ap.add_argument("--loop", type=int, default=32,
                     help="problems solved one by one for the batched comparison")
@@ -287,6 +316,8 @@ def main():
         return form_batched(args)
     if args.form == "adjoint":
         return form_vjp(args)
+    if args.form == "admm":
+        return form_admm(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -149,6 +149,25 @@ int ccm_solve_path(ccm_ctx* ctx, const double* A, int64_t n, int32_t d,
                    const ccm_options* opt, double* X, int32_t* labels, double* U,
                    ccm_stats* stats, ccm_stream_t stream);
 
+/*
+ * ccm_solve_path_admm - the same path, outputs and stopping rule as
+ * ccm_solve_path, solved by ADMM (the paper's second solver, Sec. 1, Table 3)
+ * instead of SSNAL: split z_l = (BX)_l with multiplier U and the fixed penalty
+ * options.sigma0;
+ *   X <- (I + sigma B^T B)^{-1} (A + B^T (sigma Z - U))   (CG correction, relative 1e-2),
+ *   Z <- prox_{p/sigma}(B X + U / sigma),   U <- U + sigma (B X - Z);
+ * KKT residuals and gap (definitions in ccm_stats) every 10 iterations; at most
+ * options.max_outer * options.max_newton iterations per gamma (stats[t].outer
+ * counts them, stats[t].cg the CG iterations of the X-steps). Warm-started along
+ * the path from (X, Z, U); options.precision selects the X-step CG precision.
+ * Grid engine only (options.engine is ignored).
+ */
+int ccm_solve_path_admm(ccm_ctx* ctx, const double* A, int64_t n, int32_t d,
+                        const int32_t* edges, const double* w, int64_t m,
+                        const double* gammas, int32_t T, int32_t q, double tol,
+                        const ccm_options* opt, double* X, int32_t* labels, double* U,
+                        ccm_stats* stats, ccm_stream_t stream);
+
 /* Profile of the last ccm_solve_path run with options.profile = 1 (host out). */
 int ccm_last_profile(ccm_ctx* ctx, ccm_profile* out);
 

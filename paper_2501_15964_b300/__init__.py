@@ -29,6 +29,7 @@ from .api import (  # noqa: F401
     labels,
     path_vjp,
     solve_path_batched,
+    solve_path_admm,
     last_profile,
     launch_count,
     CCMPath,

@@ -93,6 +93,32 @@ def solve_path(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U: boo
     return X, lab, U, [s.as_dict() for s in stats]
 
 
+def solve_path_admm(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U: bool = False,
+                    labels_out: bool = True, ctx: Context | None = None, raise_on_cap=False,
+                    **options):
+    """The path of solve_path by ADMM (see ccm_solve_path_admm); same returns."""
+    A = _dev(A, torch.float64, "A")
+    edges = _dev(edges, torch.int32, "edges")
+    w = _dev(w, torch.float64, "w")
+    n, d = A.shape
+    m = edges.shape[0]
+    g = [float(x) for x in gammas]
+    T = len(g)
+    ctx = ctx or default_context(A.device.index)
+    X = torch.empty((T, n, d), dtype=torch.float64, device=A.device)
+    lab = torch.empty((T, n), dtype=torch.int32, device=A.device) if labels_out else None
+    U = torch.empty((T, m, d), dtype=torch.float64, device=A.device) if return_U else None
+    stats = (Stats * T)()
+    garr = (C.c_double * T)(*g)
+    opt = make_options(**options)
+    st = load_library().ccm_solve_path_admm(ctx.handle, _ptr(A), n, d, _ptr(edges), _ptr(w), m,
+                                            garr, T, int(q), float(tol), C.byref(opt), _ptr(X),
+                                            _ptr(lab), _ptr(U), stats, _stream())
+    if st != 0 and not (st == 5 and not raise_on_cap):
+        check(st)
+    return X, lab, U, [s.as_dict() for s in stats]
+
+
 def last_profile(ctx: Context | None = None) -> dict:
     ctx = ctx or default_context()
     p = Profile()

@@ -472,6 +472,32 @@ struct RingPlan {
   bool on() const { return spans != nullptr; }
 };
 
+// Span table and scratch for one CSR when rows are long enough for the ring
+// kernels (L == 32); otherwise rp stays off and the register forms run.
+template <typename Tc>
+inline int ring_plan(Ctx* c, int L, int ld, const int64_t* off, int64_t n, RingPlan& rp,
+                     cudaStream_t s) {
+  if (L != 32) return CCM_OK;
+  rp.sh = ring_shape<Tc>(ld);
+  if (rp.sh.nw <= 0) return CCM_OK;
+  rp.nwg = c->num_sms * rp.sh.nw;
+  const size_t b_sp = round_up((int64_t)rp.nwg * sizeof(WarpSpan), 256);
+  const size_t b_cnt = round_up((int64_t)rp.nwg * 4, 256);
+  const size_t b_pd = round_up((int64_t)rp.nwg * 2 * 8, 256);
+  const size_t b_parts = (size_t)rp.nwg * 2 * ld * 8;
+  void* p;
+  CCM_TRY(ws_get(c, S_WPART, b_sp + b_cnt + b_pd + b_parts, &p));
+  char* base = (char*)p;
+  rp.spans = (WarpSpan*)base;
+  rp.cnt = (unsigned*)(base + b_sp);
+  rp.pdiag = (double*)(base + b_sp + b_cnt);
+  rp.parts = base + b_sp + b_cnt + b_pd;
+  CCM_CUDA(cudaMemsetAsync(rp.cnt, 0, b_cnt, s));
+  k_span_setup<<<(rp.nwg + 255) / 256, 256, 0, s>>>(off, n, rp.nwg, rp.spans);
+  CCM_COUNT(c);
+  return CCM_OK;
+}
+
 template <typename Tc>
 inline int set_attr_once(const void* fn, size_t smem, int device, size_t* table) {
   size_t& cur = table[device & 63];

@@ -279,25 +279,7 @@ struct GridEngine {
     // long rows: the shared-memory ring kernels over an even split of the
     // incidence stream (one span per warp)
     RingPlan rp;
-    if (L == 32) {
-      rp.sh = ring_shape<Tc>(ld);
-      if (rp.sh.nw > 0) {
-        rp.nwg = c->num_sms * rp.sh.nw;
-        const size_t b_sp = round_up((int64_t)rp.nwg * sizeof(WarpSpan), 256);
-        const size_t b_cnt = round_up((int64_t)rp.nwg * 4, 256);
-        const size_t b_pd = round_up((int64_t)rp.nwg * 2 * 8, 256);
-        const size_t b_parts = (size_t)rp.nwg * 2 * ld * 8;
-        CCM_TRY(get(S_WPART, b_sp + b_cnt + b_pd + b_parts, &p));
-        char* base = (char*)p;
-        rp.spans = (WarpSpan*)base;
-        rp.cnt = (unsigned*)(base + b_sp);
-        rp.pdiag = (double*)(base + b_sp + b_cnt);
-        rp.parts = base + b_sp + b_cnt + b_pd;
-        CCM_CUDA(cudaMemsetAsync(rp.cnt, 0, b_cnt, s));
-        k_span_setup<<<(rp.nwg + 255) / 256, 256, 0, s>>>(off, n, rp.nwg, rp.spans);
-        CCM_COUNT(c);
-      }
-    }
+    CCM_TRY(ring_plan<Tc>(c, L, ld, off, n, rp, s));
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     k_pad_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld);
     CCM_COUNT(c);

@@ -557,6 +557,9 @@ __global__ void __launch_bounds__(256)
 k_kkt_node(const double* __restrict__ X, const double* __restrict__ Ap,
            const double* __restrict__ G, int64_t total, double* partials, Ctl* ctl);
 
+// ||v||^2 -> ctl->dots[1]
+__global__ void k_sumsq(const double* __restrict__ v, int64_t total, double* partials, Ctl* ctl);
+
 // ------------------------------------------------------------ layout
 __global__ void k_pad_rows(const double* __restrict__ src, double* __restrict__ dst, int64_t rows,
                            int d, int ld);
