@@ -263,8 +263,8 @@ def form_vjp(args):
 
 
 def form_admm(args):
-    """ADMM (the paper's second solver) against SSNAL on the same GPU, grid
-    engine, same tolerance: the n = 200, d = 2 workload (20 gammas)."""
+    """ADMM and fast AMA (the paper's other two solvers) against SSNAL on the
+    same GPU, grid engine, same tolerance: the n = 200, d = 2 workload (20 gammas)."""
     import torch
     import paper_2501_15964_b300 as ccm
     torch.cuda.set_device(0)
@@ -274,7 +274,8 @@ def form_admm(args):
     At = torch.tensor(A, device="cuda")
     E, w, _ = ccm.build_graph(At, wl.k, wl.phi)
     runs = {}
-    for name, fn in (("ssnal", ccm.solve_path), ("admm", ccm.solve_path_admm)):
+    for name, fn in (("ssnal", ccm.solve_path), ("admm", ccm.solve_path_admm),
+                     ("ama", ccm.solve_path_ama)):
         fn(At, E, w, gam, tol=SOLVE_TOL, engine=1)
         ms, (_, _, _, st) = _time(lambda: fn(At, E, w, gam, tol=SOLVE_TOL, engine=1), stream,
                                   args.steps)
@@ -282,10 +283,11 @@ def form_admm(args):
                       "iterations": sum(s["outer"] for s in st), "cg": sum(s["cg"] for s in st),
                       "max_kkt": max(s["kkt"] for s in st), "max_gap": max(s["gap"] for s in st),
                       "not_converged": sum(1 for s in st if s["status"] != 0)}
-    line = {"form": "admm", "metric": "gamma-solves/s, ADMM vs SSNAL (grid engine)",
+    line = {"form": "admm", "metric": "gamma-solves/s, SSNAL vs ADMM vs fast AMA (grid engine)",
             "unit": "gamma-solves/s", "workload": "gmm200_d2", "gammas": len(gam),
-            "tol": SOLVE_TOL, "ssnal": runs["ssnal"], "admm": runs["admm"],
-            "ssnal_over_admm": runs["admm"]["ms"] / runs["ssnal"]["ms"]}
+            "tol": SOLVE_TOL, "ssnal": runs["ssnal"], "admm": runs["admm"], "ama": runs["ama"],
+            "ssnal_over_admm": runs["admm"]["ms"] / runs["ssnal"]["ms"],
+            "ssnal_over_ama": runs["ama"]["ms"] / runs["ssnal"]["ms"]}
     print(json.dumps(line), flush=True)
     return 0
 

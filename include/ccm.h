@@ -168,6 +168,23 @@ int ccm_solve_path_admm(ccm_ctx* ctx, const double* A, int64_t n, int32_t d,
                         const ccm_options* opt, double* X, int32_t* labels, double* U,
                         ccm_stats* stats, ccm_stream_t stream);
 
+/*
+ * ccm_solve_path_ama - the same path, outputs and stopping rule as
+ * ccm_solve_path, solved by fast AMA (the paper's third solver, Sec. 1, Table 3):
+ * projected gradient ascent on the dual with Nesterov momentum and gradient
+ * restart, X(U) = A - B^T U,
+ *   U <- Pi(Uh + nu B X(Uh)),  Uh = U + momentum,  nu = 1 / max_l (deg_i + deg_j);
+ * KKT residuals and gap every 10 iterations (eta_d is 0 by construction); at most
+ * 10 * options.max_outer * options.max_newton iterations per gamma (stats[t].outer
+ * counts them; stats[t].sigma reports nu). Warm-started along the path from U.
+ * Grid engine only; options.precision and options.engine are ignored (float64).
+ */
+int ccm_solve_path_ama(ccm_ctx* ctx, const double* A, int64_t n, int32_t d,
+                       const int32_t* edges, const double* w, int64_t m,
+                       const double* gammas, int32_t T, int32_t q, double tol,
+                       const ccm_options* opt, double* X, int32_t* labels, double* U,
+                       ccm_stats* stats, ccm_stream_t stream);
+
 /* Profile of the last ccm_solve_path run with options.profile = 1 (host out). */
 int ccm_last_profile(ccm_ctx* ctx, ccm_profile* out);
 

@@ -30,6 +30,7 @@ from .api import (  # noqa: F401
     path_vjp,
     solve_path_batched,
     solve_path_admm,
+    solve_path_ama,
     last_profile,
     launch_count,
     CCMPath,

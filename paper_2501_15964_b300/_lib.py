@@ -69,6 +69,9 @@ _SIGS = {
     "ccm_solve_path_admm": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, C.c_int64,
                                       C.POINTER(C.c_double), C.c_int32, C.c_int32, C.c_double,
                                       C.POINTER(Options), _P, _P, _P, C.POINTER(Stats), _P]),
+    "ccm_solve_path_ama": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, C.c_int64,
+                                     C.POINTER(C.c_double), C.c_int32, C.c_int32, C.c_double,
+                                     C.POINTER(Options), _P, _P, _P, C.POINTER(Stats), _P]),
     "ccm_last_profile": (C.c_int, [_P, C.POINTER(Profile)]),
     "ccm_launch_count": (C.c_int64, [_P]),
     "ccm_labels": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, C.c_int64, _P,

@@ -97,6 +97,20 @@ def solve_path_admm(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U
                     labels_out: bool = True, ctx: Context | None = None, raise_on_cap=False,
                     **options):
     """The path of solve_path by ADMM (see ccm_solve_path_admm); same returns."""
+    return _solve_path_with("ccm_solve_path_admm", A, edges, w, gammas, tol, q, return_U,
+                            labels_out, ctx, raise_on_cap, options)
+
+
+def solve_path_ama(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U: bool = False,
+                   labels_out: bool = True, ctx: Context | None = None, raise_on_cap=False,
+                   **options):
+    """The path of solve_path by fast AMA (see ccm_solve_path_ama); same returns."""
+    return _solve_path_with("ccm_solve_path_ama", A, edges, w, gammas, tol, q, return_U,
+                            labels_out, ctx, raise_on_cap, options)
+
+
+def _solve_path_with(entry, A, edges, w, gammas, tol, q, return_U, labels_out, ctx, raise_on_cap,
+                     options):
     A = _dev(A, torch.float64, "A")
     edges = _dev(edges, torch.int32, "edges")
     w = _dev(w, torch.float64, "w")
@@ -111,9 +125,9 @@ def solve_path_admm(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U
     stats = (Stats * T)()
     garr = (C.c_double * T)(*g)
     opt = make_options(**options)
-    st = load_library().ccm_solve_path_admm(ctx.handle, _ptr(A), n, d, _ptr(edges), _ptr(w), m,
-                                            garr, T, int(q), float(tol), C.byref(opt), _ptr(X),
-                                            _ptr(lab), _ptr(U), stats, _stream())
+    st = getattr(load_library(), entry)(ctx.handle, _ptr(A), n, d, _ptr(edges), _ptr(w), m, garr,
+                                        T, int(q), float(tol), C.byref(opt), _ptr(X), _ptr(lab),
+                                        _ptr(U), stats, _stream())
     if st != 0 and not (st == 5 and not raise_on_cap):
         check(st)
     return X, lab, U, [s.as_dict() for s in stats]

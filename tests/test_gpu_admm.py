@@ -1,5 +1,6 @@
-"""GPU ADMM (ccm_solve_path_admm, the paper's second solver, Sec. 1) against the
-CPU oracle: the same bar as the SSNAL path — X within 1e-6 relative of the
+"""GPU ADMM and fast AMA (ccm_solve_path_admm / ccm_solve_path_ama, the paper's
+second and third solvers, Sec. 1) against the CPU oracle: the same bar as the
+SSNAL path — X within 1e-6 relative of the
 oracle solved to KKT <= 1e-11, the KKT residuals and relative gap recomputed by
 the oracle from the GPU's (X, U) <= 1e-6, labels equal to the oracle's
 labelling of the GPU's X — on short rows and on long rows (the ring kernels)."""
@@ -25,14 +26,14 @@ def ccm():
     return m
 
 
-def _check(ccm, A, E, w, gammas, precision):
+def _check(ccm, A, E, w, gammas, precision, solver="admm"):
     Xo, _, _ = ossnal.solve_path(A, E, w, gammas, tol=1e-11)
     dev = torch.device("cuda:0")
     At = torch.tensor(A, device=dev)
     Et = torch.tensor(E, dtype=torch.int32, device=dev)
     wt = torch.tensor(w, device=dev)
-    X, lab, U, st = ccm.solve_path_admm(At, Et, wt, gammas, tol=SOLVE_TOL, return_U=True,
-                                        precision=precision)
+    fn = ccm.solve_path_admm if solver == "admm" else ccm.solve_path_ama
+    X, lab, U, st = fn(At, Et, wt, gammas, tol=SOLVE_TOL, return_U=True, precision=precision)
     X, U, lab = X.cpu().numpy(), U.cpu().numpy(), lab.cpu().numpy()
     for t, g in enumerate(gammas):
         assert st[t]["status"] == 0, st[t]
@@ -60,3 +61,17 @@ def test_admm_long_rows_matches_oracle(ccm, precision):
     A = cent[rng.integers(0, 3, 48)] + rng.normal(size=(48, 150))
     E, w, _ = ograph.build_graph(A, 5, 0.0)
     _check(ccm, A, E, w, np.array([1.0, 8.0]), precision)
+
+
+def test_ama_gmm200_matches_oracle(ccm):
+    A, _, wl = synth.make_workload("gmm200_d2", 0, n=120)
+    E, w, _ = ograph.build_graph(A, wl.k, wl.phi)
+    _check(ccm, A, E, w, np.array([0.0, 0.05, 0.5, 3.0]), 0, solver="ama")
+
+
+def test_ama_long_rows_matches_oracle(ccm):
+    rng = np.random.default_rng(5)
+    cent = rng.normal(0, 2, size=(3, 150))
+    A = cent[rng.integers(0, 3, 48)] + rng.normal(size=(48, 150))
+    E, w, _ = ograph.build_graph(A, 5, 0.0)
+    _check(ccm, A, E, w, np.array([1.0, 8.0]), 0, solver="ama")
