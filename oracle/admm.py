@@ -1,4 +1,4 @@
-"""Model CCM (q = 2) by ADMM (oracle cross-check).
+"""Model CCM (q = 2 or q = 1) by ADMM (oracle cross-check).
 
 ADMM is one of the three solvers the paper's package offers (Sec. 1, Table 1,
 Table 3). Here it is a second, independent route to the unique minimiser X*,
@@ -18,12 +18,12 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .kkt import incidence, kkt, prox_group
+from .kkt import incidence, kkt, prox_group, prox_l1
 
 __all__ = ["solve"]
 
 
-def solve(A, edges, w, gamma, sigma=1.0, tol=1e-10, max_iter=200000, check_every=50):
+def solve(A, edges, w, gamma, sigma=1.0, tol=1e-10, max_iter=200000, check_every=50, q=2):
     A = np.asarray(A, dtype=np.float64)
     edges = np.asarray(edges, dtype=np.int64)
     n, d = A.shape
@@ -39,13 +39,13 @@ def solve(A, edges, w, gamma, sigma=1.0, tol=1e-10, max_iter=200000, check_every
         rhs = A + B.T @ (sigma * Z - U)
         X = np.column_stack([solve_x(rhs[:, c]) for c in range(d)])
         BX = B @ X
-        Z = prox_group(BX + U / sigma, r / sigma)
+        Z = (prox_l1 if q == 1 else prox_group)(BX + U / sigma, r / sigma)
         U = U + sigma * (BX - Z)
         if it % check_every == 0:
-            res = kkt(A, edges, w, gamma, X, U)
+            res = kkt(A, edges, w, gamma, X, U, q)
             if res["kkt"] <= tol and res["gap"] <= tol:
                 break
     if res is None:
-        res = kkt(A, edges, w, gamma, X, U)
+        res = kkt(A, edges, w, gamma, X, U, q)
     res["iters"] = it
     return X, U, res

@@ -1,4 +1,4 @@
-"""Optimality measures for model CCM with q = 2 (oracle).
+"""Optimality measures for model CCM with q = 2 or q = 1 (oracle).
 
 Notation. For edges l = (i, j), i < j: (BX)_l = x_i - x_j; r_l = gamma * w_l;
 p(Z) = sum_l r_l ||z_l||_2. The primal is min_X 1/2||X - A||^2 + p(BX) (model
@@ -12,6 +12,9 @@ Readings (the paper gives only the gap of Sec. 4):
 * gap   = |f_p - f_d| / (1 + |f_p| + |f_d|)             (Sec. 4)
 * kkt   = max(eta_D, eta_P)
 
+For q = 1 the penalty is p(Z) = sum_l r_l ||z_l||_1, the dual ball is
+||u_l||_inf <= r_l and prox_p is the elementwise soft threshold.
+
 Pinned by: weak duality (gap >= 0 whenever U is feasible), exact zeros at the
 closed-form n = 2 solution and at gamma = 0, and agreement of two independent
 solvers (tests/test_oracle_solvers.py).
@@ -21,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["incidence", "prox_group", "kkt"]
+__all__ = ["incidence", "prox_group", "prox_l1", "kkt"]
 
 
 def incidence(edges: np.ndarray, n: int) -> sp.csr_matrix:
@@ -42,7 +45,12 @@ def prox_group(V: np.ndarray, r: np.ndarray) -> np.ndarray:
     return V * scale[:, None]
 
 
-def kkt(A, edges, w, gamma, X, U):
+def prox_l1(V: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """Elementwise prox of r_l ||.||_1: soft threshold of row l at r_l."""
+    return np.sign(V) * np.maximum(np.abs(V) - r[:, None], 0.0)
+
+
+def kkt(A, edges, w, gamma, X, U, q=2):
     """Residuals and objectives at (X, U); returns a dict."""
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -52,10 +60,16 @@ def kkt(A, edges, w, gamma, X, U):
     BtU = B.T @ U
     nA = np.linalg.norm(A)
     eta_d = np.linalg.norm(X - A + BtU) / (1.0 + nA)
-    eta_p = np.linalg.norm(BX - prox_group(BX + U, r)) / (1.0 + nA)
-    fp = 0.5 * np.sum((X - A) ** 2) + np.sum(r * np.sqrt(np.sum(BX * BX, axis=1)))
+    if q == 1:
+        eta_p = np.linalg.norm(BX - prox_l1(BX + U, r)) / (1.0 + nA)
+        pen = np.sum(r * np.sum(np.abs(BX), axis=1))
+        nu = np.max(np.abs(U), axis=1) if U.size else np.zeros(0)
+    else:
+        eta_p = np.linalg.norm(BX - prox_group(BX + U, r)) / (1.0 + nA)
+        pen = np.sum(r * np.sqrt(np.sum(BX * BX, axis=1)))
+        nu = np.sqrt(np.sum(U * U, axis=1))
+    fp = 0.5 * np.sum((X - A) ** 2) + pen
     fd = np.sum(A * BtU) - 0.5 * np.sum(BtU * BtU)
-    nu = np.sqrt(np.sum(U * U, axis=1))
     infeas = float(np.max(np.maximum(nu - r, 0.0))) if nu.size else 0.0
     gap = abs(fp - fd) / (1.0 + abs(fp) + abs(fd))
     return dict(eta_d=float(eta_d), eta_p=float(eta_p), kkt=float(max(eta_d, eta_p)),

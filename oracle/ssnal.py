@@ -35,9 +35,22 @@ from .kkt import incidence, kkt
 __all__ = ["solve", "solve_path"]
 
 
-def _eval(X, A, U, B, r, sigma):
-    """phi (without its X-independent term), grad phi, Pi(y), y, ||y_l||."""
+def _eval(X, A, U, B, r, sigma, q=2):
+    """phi (without its X-independent term), grad phi, Pi(y), y, ||y_l||.
+
+    For q = 1 the ball is ||u_l||_inf <= r_l: Pi clamps each element to
+    [-r_l, r_l], h is the elementwise Huber function, and the last return is |y|.
+    """
     Y = U + sigma * (B @ X)
+    if q == 1:
+        ay = np.abs(Y)
+        rr = r[:, None]
+        hin = ay <= rr
+        h = np.where(hin, 0.5 * Y * Y, rr * ay - 0.5 * rr * rr)
+        phi = 0.5 * np.sum((X - A) ** 2) + np.sum(h) / sigma
+        PiY = np.clip(Y, -rr, rr)
+        G = X - A + B.T @ PiY
+        return phi, G, PiY, Y, ay
     ny = np.sqrt(np.sum(Y * Y, axis=1))
     inside = ny <= r
     h = np.where(inside, 0.5 * ny * ny, r * ny - 0.5 * r * r)
@@ -48,6 +61,11 @@ def _eval(X, A, U, B, r, sigma):
     PiY = Y * scale[:, None]
     G = X - A + B.T @ PiY
     return phi, G, PiY, Y, ny
+
+
+def _mask_l1(ay, r):
+    """q = 1: P_l = diag(mask_l), mask = 1 where |y_k| <= r_l (and r_l > 0)."""
+    return ((ay <= r[:, None]) & (r[:, None] > 0)).astype(np.float64)
 
 
 def _jacobian_parts(Y, ny, r):
@@ -62,19 +80,24 @@ def _jacobian_parts(Y, ny, r):
     return alpha, yhat
 
 
-def _apply_V(Dv, B, alpha, yhat, sigma):
+def _apply_V(Dv, B, alpha, yhat, sigma, mask=None):
     BD = B @ Dv
+    if mask is not None:
+        return Dv + sigma * (B.T @ (mask * BD))
     s = np.sum(yhat * BD, axis=1)
     PBD = alpha[:, None] * (BD - s[:, None] * yhat)
     return Dv + sigma * (B.T @ PBD)
 
 
-def _dense_V(n, d, edges, alpha, yhat, sigma):
+def _dense_V(n, d, edges, alpha, yhat, sigma, mask=None):
     V = np.eye(n * d)
     for l in range(edges.shape[0]):
-        if alpha[l] == 0.0:
+        if mask is not None:
+            P = np.diag(mask[l])
+        elif alpha[l] == 0.0:
             continue
-        P = alpha[l] * (np.eye(d) - np.outer(yhat[l], yhat[l]))
+        else:
+            P = alpha[l] * (np.eye(d) - np.outer(yhat[l], yhat[l]))
         i, j = edges[l]
         si, sj = slice(i * d, i * d + d), slice(j * d, j * d + d)
         V[si, si] += sigma * P
@@ -84,13 +107,13 @@ def _dense_V(n, d, edges, alpha, yhat, sigma):
     return V
 
 
-def _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method, cg_rtol):
+def _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method, cg_rtol, mask=None):
     if method == "dense":
-        V = _dense_V(n, d, edges, alpha, yhat, sigma)
+        V = _dense_V(n, d, edges, alpha, yhat, sigma, mask)
         return np.linalg.solve(V, -G.reshape(-1)).reshape(n, d), 0
     op = spla.LinearOperator(
         (n * d, n * d),
-        matvec=lambda v: _apply_V(v.reshape(n, d), B, alpha, yhat, sigma).reshape(-1),
+        matvec=lambda v: _apply_V(v.reshape(n, d), B, alpha, yhat, sigma, mask).reshape(-1),
         dtype=np.float64)
     it = [0]
 
@@ -103,8 +126,8 @@ def _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method, cg_rtol):
 
 
 def solve(A, edges, w, gamma, X0=None, U0=None, sigma0=1.0, tol=1e-11,
-          max_outer=300, max_newton=60, method=None, sigma_max=1e4):
-    """Solve model CCM at one gamma. Returns (X, U, sigma, info)."""
+          max_outer=300, max_newton=60, method=None, sigma_max=1e4, q=2):
+    """Solve model CCM (q = 2 or q = 1) at one gamma. Returns (X, U, sigma, info)."""
     A = np.asarray(A, dtype=np.float64)
     edges = np.asarray(edges, dtype=np.int64)
     n, d = A.shape
@@ -120,28 +143,33 @@ def solve(A, edges, w, gamma, X0=None, U0=None, sigma0=1.0, tol=1e-11,
     info = dict(outer=0, newton=0, cg=0, ls=0)
     last_kkt = 1.0
     last_etap = None
-    res = kkt(A, edges, w, gamma, X, U)
+    res = kkt(A, edges, w, gamma, X, U, q)
     if res["kkt"] <= tol and res["gap"] <= tol:
         info.update(res)
         return X, U, sigma, info
     for outer in range(max_outer):
         eps_in = max(0.5 * tol, 0.1 * last_kkt)
-        phi, G, PiY, Y, ny = _eval(X, A, U, B, r, sigma)
+        phi, G, PiY, Y, ny = _eval(X, A, U, B, r, sigma, q)
         for _ in range(max_newton):
             if np.linalg.norm(G) / (1.0 + nA) <= eps_in:
                 break
-            alpha, yhat = _jacobian_parts(Y, ny, r)
+            mask = None
+            if q == 1:
+                mask = _mask_l1(ny, r)
+                alpha = yhat = None
+            else:
+                alpha, yhat = _jacobian_parts(Y, ny, r)
             gn = np.linalg.norm(G)
             cg_rtol = max(1e-14, min(1e-3, 1e-2 * gn / (1.0 + nA)))
             Dv, cgit = _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method,
-                                         cg_rtol)
+                                         cg_rtol, mask)
             info["cg"] += cgit
             gd = float(np.sum(G * Dv))
             t = 1.0
             slack = 1e-14 * (1.0 + abs(phi))
             while True:
                 Xt = X + t * Dv
-                phit, Gt, PiYt, Yt, nyt = _eval(Xt, A, U, B, r, sigma)
+                phit, Gt, PiYt, Yt, nyt = _eval(Xt, A, U, B, r, sigma, q)
                 info["ls"] += 1
                 if phit <= phi + 1e-4 * t * gd + slack or t < 1e-10:
                     break
@@ -152,7 +180,7 @@ def solve(A, edges, w, gamma, X0=None, U0=None, sigma0=1.0, tol=1e-11,
                 break
         U = PiY
         info["outer"] += 1
-        res = kkt(A, edges, w, gamma, X, U)
+        res = kkt(A, edges, w, gamma, X, U, q)
         if res["kkt"] <= tol and res["gap"] <= tol:
             break
         if last_etap is not None and res["eta_p"] > 0.2 * last_etap:

@@ -155,7 +155,7 @@ def test_weak_duality_and_gap():
 
 def test_planted_sign_error_is_caught(monkeypatch):
     """A plausible mistake (wrong sign of B^T in the gradient) must fail a pin."""
-    def bad_eval(X, A, U, B, r, sigma):
+    def bad_eval(X, A, U, B, r, sigma, q=2):
         Y = U + sigma * (B @ X)
         ny = np.sqrt(np.sum(Y * Y, axis=1))
         inside = ny <= r
@@ -171,3 +171,57 @@ def test_planted_sign_error_is_caught(monkeypatch):
                              max_outer=20)
     want = np.stack([a[0] - 0.8 * (a[0] - a[1]) / 5, a[1] + 0.8 * (a[0] - a[1]) / 5])
     assert not np.allclose(X, want, atol=1e-6)
+
+
+# ---------------------------------------------------------------- q = 1
+def test_two_points_closed_form_q1():
+    """n = 2, q = 1: x1 - x2 = soft(a1 - a2, 2 r) per coordinate, x1 + x2 = a1 + a2."""
+    a = np.array([[1.0, 2.0, 0.5], [4.0, -2.0, 0.3]])
+    E = np.array([[0, 1]])
+    w = np.array([0.8])
+    for gamma in [0.05, 0.5, 1.0, 3.0]:
+        r = gamma * w[0]
+        D = a[0] - a[1]
+        delta = np.sign(D) * np.maximum(np.abs(D) - 2 * r, 0.0)
+        mid = a.mean(0)
+        want = np.stack([mid + 0.5 * delta, mid - 0.5 * delta])
+        X, U, _, info = ssnal.solve(a, E, w, gamma, tol=1e-13, q=1)
+        np.testing.assert_allclose(X, want, atol=1e-11)
+        assert info["kkt"] <= 1e-12
+        res = kkt.kkt(a, E, w, gamma, X, U, q=1)
+        assert res["dual_infeas"] <= 1e-12
+
+
+@pytest.mark.parametrize("gamma", [0.005, 0.03, 0.2])
+def test_q1_complete_graph_is_three_exact_1d_paths(gamma):
+    """q = 1 separates by coordinate: on the complete graph with unit weights each
+    column is the certified exact 1-D solution of that column."""
+    a = np.random.default_rng(4).normal(size=(16, 3))
+    E = exact1d.complete_graph(16)
+    w = np.ones(E.shape[0])
+    X, _, _, info = ssnal.solve(a, E, w, gamma, tol=1e-12, q=1)
+    for k in range(3):
+        np.testing.assert_allclose(X[:, k], exact1d.solve(a[:, k], gamma), atol=1e-10)
+
+
+def test_ssnal_matches_admm_q1():
+    A, edges, w = _small_problem(seed=12, n=30, d=3, k=5)
+    for g in [0.05, 0.4, 2.0]:
+        X, _, _, info = ssnal.solve(A, edges, w, g, tol=1e-12, q=1)
+        Xa, _, ra = admm.solve(A, edges, w, g, tol=1e-11, max_iter=50000, q=1)
+        assert info["kkt"] <= 1e-11
+        np.testing.assert_allclose(X, Xa, atol=1e-8)
+
+
+def test_weak_duality_q1():
+    """f_d(U) <= f_p(X) for every X and every U with ||u_l||_inf <= r_l."""
+    A, edges, w = _small_problem(seed=13, n=25, d=3, k=4)
+    rng = np.random.default_rng(14)
+    g = 0.4
+    r = g * w
+    for _ in range(20):
+        X = A + rng.normal(size=A.shape)
+        U = rng.uniform(-1, 1, size=(edges.shape[0], 3)) * r[:, None]
+        res = kkt.kkt(A, edges, w, g, X, U, q=1)
+        assert res["fd"] <= res["fp"] + 1e-12
+        assert res["dual_infeas"] == 0.0
