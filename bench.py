@@ -292,6 +292,36 @@ def form_admm(args):
     return 0
 
 
+def form_q1(args):
+    """Model CCM with q = 1 (l1 norm on x_i - x_j) against q = 2 on the bench
+    workload: graph build + path, same tolerance, device-resident."""
+    import torch
+    import paper_2501_15964_b300 as ccm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    A, wl, gam = make_problem(0)
+    if args.n_gamma > 0:
+        gam = gam[: args.n_gamma]
+    At = torch.tensor(A, device="cuda")
+    out = {}
+    for q in (2, 1):
+        def step():
+            E, w, _ = ccm.build_graph(At, wl.k, wl.phi)
+            return ccm.solve_path(At, E, w, gam, q=q, tol=SOLVE_TOL)
+        step()
+        ms, (_, _, _, st) = _time(step, stream, args.steps)
+        out[f"q{q}"] = {"value": len(gam) / (ms / 1000.0), "ms": ms,
+                        "newton": sum(s["newton"] for s in st), "cg": sum(s["cg"] for s in st),
+                        "max_kkt": max(s["kkt"] for s in st), "max_gap": max(s["gap"] for s in st),
+                        "not_converged": sum(1 for s in st if s["status"] != 0),
+                        "clusters_last_gamma": st[-1]["n_clusters"]}
+    line = {"form": "q1", "metric": "gamma-solves/s, q = 1 vs q = 2 (graph build + path)",
+            "unit": "gamma-solves/s", "workload": WORKLOAD, "gammas": len(gam), "tol": SOLVE_TOL,
+            **out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,9 +336,10 @@ def main():
                     help="solve only the first N gammas of the path (profiling runs)")
     ap.add_argument("--gamma-from", type=int, default=0,
                     help="start the path at this index of the gamma grid, cold (profiling runs)")
-    ap.add_argument("--form", default="path", choices=["path", "batched", "adjoint", "admm"],
-                    help="path (default, the JSON contract line), or the batched, adjoint or "
-                         "ADMM comparison")
+    ap.add_argument("--form", default="path",
+                    choices=["path", "batched", "adjoint", "admm", "q1"],
+                    help="path (default, the JSON contract line), or the batched, adjoint, "
+                         "ADMM / fast AMA or q = 1 comparison")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched form")
     ap.add_argument("--loop", type=int, default=32,
                     help="problems solved one by one for the batched comparison")
@@ -320,6 +351,8 @@ def main():
         return form_vjp(args)
     if args.form == "admm":
         return form_admm(args)
+    if args.form == "q1":
+        return form_q1(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

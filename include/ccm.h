@@ -133,13 +133,16 @@ int ccm_build_graph(ccm_ctx* ctx, const double* A, int64_t n, int32_t d, int32_t
  * along the path (Sec. 1: 0 <= gamma_1 < ... < gamma_T).
  *
  * A: n x d; edges: m x 2 (see conventions); w: m float64 >= 0;
- * gammas: HOST array of T non-decreasing values >= 0; q must be 2 (others:
- * CCM_ERR_UNSUPPORTED); tol > 0: stop each gamma when max(eta_d, eta_p) <= tol
+ * gammas: HOST array of T non-decreasing values >= 0; q = 2 (the Euclidean norm
+ * of x_i - x_j) or q = 1 (its l1 norm: the dual ball becomes ||u_l||_inf <= r_l,
+ * the Newton Jacobian a 0/1 diagonal per edge; grid engine only), others
+ * CCM_ERR_UNSUPPORTED; tol > 0: stop each gamma when max(eta_d, eta_p) <= tol
  * and the relative duality gap of Sec. 4 is <= tol (definitions in ccm_stats).
  * Outputs: X: T x n x d float64; labels: T x n int32 or NULL (label = rank of the
  * cluster's smallest node index; an edge is fused when the float64 squared
  * distance of its endpoints, summed in feature order without FMA, is <= 1e-12);
  * U: T x m x d float64 or NULL (final multipliers); stats: HOST array of T or NULL.
+ * For q = 1, eta_p uses prox of r_l ||.||_1 (soft threshold) and f_p r_l ||.||_1.
  * Returns CCM_ERR_NOT_CONVERGED if any gamma hit an iteration cap (all outputs
  * are still written; stats[t].status says which).
  */

@@ -331,8 +331,13 @@ struct GridEngine {
 
     // evaluate phi, grad phi, Pi(y), yhat, alpha at Xc (one edge pass + one node pass)
     auto evaluate = [&](const double* Xc, double* phi, double* gn, double* nout) -> int {
-      k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
-                                                        Ut, Yh, alpha, kind, m, ld, part, ctl);
+      if (a.q == 1)
+        k_edge_eval_q1<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
+                                                             Ut, Yh, alpha, kind, m, d, ld, part,
+                                                             ctl);
+      else
+        k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
+                                                          Ut, Yh, alpha, kind, m, ld, part, ctl);
       CCM_COUNT(c);
       CCM_TRY(launch_node_grad<L, CH, Tc>(c, Xc, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv,
                                           rp, n, ld, part, ctl, s));
@@ -431,8 +436,14 @@ struct GridEngine {
         // multiplier update: U <- Pi(U + sigma B X) (computed at the last evaluation)
         std::swap(U, Ut);
         // KKT at (X, U) fused with the edge part of the next evaluation at (X, U)
-        k_kkt_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma, Ut,
-                                                              Yh, alpha, kind, m, ld, part, ctl);
+        if (a.q == 1)
+          k_kkt_edge_eval_q1<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma,
+                                                                   Ut, Yh, alpha, kind, m, d, ld,
+                                                                   part, ctl);
+        else
+          k_kkt_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma,
+                                                                Ut, Yh, alpha, kind, m, ld, part,
+                                                                ctl);
         CCM_COUNT(c);
         edge_ready = true;
         edge_sigma = sigma;
@@ -532,8 +543,8 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     set_error("ccm_solve_path: invalid argument");
     return CCM_ERR_INVALID_ARG;
   }
-  if (q != 2) {
-    set_error("ccm_solve_path: only q = 2 is implemented (got q = %d)", q);
+  if (q != 2 && q != 1) {
+    set_error("ccm_solve_path: q = 1 and q = 2 are implemented (got q = %d)", q);
     return CCM_ERR_UNSUPPORTED;
   }
   if (d > ccm_max_dim()) {
@@ -564,16 +575,17 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
   SolveArgs a;
   a.A = A; a.n = n; a.d = d; a.edges = edges; a.w = w; a.m = m;
   a.gammas = gammas; a.T = T; a.tol = tol; a.opt = o; a.Xout = X; a.Uout = U;
-  a.stats = stats; a.X0 = o.X0; a.U0 = o.U0;
+  a.stats = stats; a.X0 = o.X0; a.U0 = o.U0; a.q = q;
   c->last_profile = ccm_profile{};
   const int64_t launches0 = c->launches;
   // small problems: one thread block runs the whole path (no host round trips);
   // otherwise the grid engine spreads every phase over the whole GPU
   const int64_t ldd = round_up(d, 4);
   const bool small = n * ldd <= 16384 && m * ldd <= 131072 && d <= 128;
-  const bool use_block = o.engine == CCM_ENGINE_BLOCK || (o.engine == CCM_ENGINE_AUTO && small);
-  if (o.engine == CCM_ENGINE_BLOCK && d > 128) {
-    set_error("ccm_solve_path: the block engine supports d <= 128");
+  const bool use_block =
+      o.engine == CCM_ENGINE_BLOCK || (o.engine == CCM_ENGINE_AUTO && small && q == 2);
+  if (o.engine == CCM_ENGINE_BLOCK && (d > 128 || q != 2)) {
+    set_error("ccm_solve_path: the block engine supports q = 2 and d <= 128");
     return CCM_ERR_UNSUPPORTED;
   }
   if (use_block) {

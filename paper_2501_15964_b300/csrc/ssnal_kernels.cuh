@@ -20,7 +20,9 @@
 
 namespace ccm {
 
-enum EdgeKind : uint8_t { K_INERT = 0, K_IN = 1, K_OUT = 2 };
+// K_MASK (q = 1 only): P_l = diag(mask) with mask_k = 1 where |y_k| <= r_l; the
+// mask row is stored in the yhat slot and alpha holds trace(P_l)/d.
+enum EdgeKind : uint8_t { K_INERT = 0, K_IN = 1, K_OUT = 2, K_MASK = 3 };
 
 // Device-resident scalars of one solve (one problem).
 struct CgCtl {
@@ -194,7 +196,9 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
       for (int64_t t = b; t < eend; ++t) {
         const int e = inc[t].x;
         const uint8_t kd = kind[e];
-        diag += kd == K_IN ? 1.0 : (kd == K_OUT ? (double)alpha[e] * tr_out : 0.0);
+        diag += kd == K_IN ? 1.0
+                : (kd == K_OUT ? (double)alpha[e] * tr_out
+                               : (kd == K_MASK ? (double)alpha[e] : 0.0));
       }
       Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
     }
@@ -219,7 +223,8 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
 
 // Per-incidence operator coefficients, packed once per Newton step: c = 1
 // (inside edge, P_l = I), c = -alpha_l (outside edge, P_l = alpha_l (I - yhat yhat^T)),
-// c = 0 (inert edge); mo = Minv of the incidence's other endpoint.
+// c = 2 (q = 1 mask edge, P_l = diag(mask row)), c = 0 (inert edge); mo = Minv of
+// the incidence's other endpoint.
 template <typename Tc>
 struct alignas(2 * sizeof(Tc)) IncMeta {
   Tc c, mo;
@@ -250,7 +255,7 @@ k_cg_init(const double* __restrict__ G, const Tc* __restrict__ Minv, Tc* __restr
       const int2 eo = inc[t];
       const uint8_t kd = kind[eo.x];
       IncMeta<Tc> mm;
-      mm.c = kd == K_IN ? (Tc)1 : (kd == K_OUT ? -alpha[eo.x] : (Tc)0);
+      mm.c = kd == K_IN ? (Tc)1 : (kd == K_OUT ? -alpha[eo.x] : (kd == K_MASK ? (Tc)2 : (Tc)0));
       mm.mo = Minv[eo.y];
       meta[t] = mm;
     }
@@ -334,7 +339,14 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
       for (int c = 0; c < CH; ++c)
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[c][k] = u[c][k] - mm.mo * v[c][k];
-      if (mm.c < (Tc)0) {
+      if (mm.c > (Tc)1.5) {  // q = 1: diagonal mask
+        Tc mk[CH][4];
+        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, mk);
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) accv[c][k] += mk[c][k] * v[c][k];
+      } else if (mm.c < (Tc)0) {
         Tc yh[CH][4];
         row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, yh);
         Tc s = (Tc)0;
@@ -542,6 +554,134 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
         for (int k = 0; k < 4; ++k) yh[c][k] = to_operator<Tc>(y[c][k]) * invc;
       row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
     }
+  }
+  double tot[4];
+  if (grid_reduce<4>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {
+    ctl->kkt[0] = tot[0];
+    ctl->kkt[1] = tot[1];
+    ctl->eval[0] = tot[2];
+    ctl->eval[3] = tot[3];
+  }
+}
+
+// ------------------------------------------------------------ q = 1
+// Model CCM with the l1 norm on the differences (Sec. 1 allows any q >= 1): the
+// ball of the dual is ||u_l||_inf <= r_l, so Pi clamps each element to
+// [-r_l, r_l], h_l(y) = sum_k huber_{r_l}(y_k), and P_l = diag(mask) with mask_k =
+// 1 where |y_k| <= r_l. Per edge: Pi(y) -> Ut, the mask row -> Yh (stored only
+// when some element is clamped: kind K_MASK, alpha = trace(P_l)/d), kind K_IN when
+// no element is clamped, K_INERT when r_l = 0. Returns the number of elements
+// still inside, for the caller.
+template <int LANES, int CH, typename Tc>
+__device__ __forceinline__ void q1_edge_outputs(const double (&y)[CH][4], double r, int d,
+                                                int lane, int ld, unsigned mask, int64_t e,
+                                                double* __restrict__ Ut, Tc* __restrict__ Yh,
+                                                Tc* __restrict__ alpha,
+                                                uint8_t* __restrict__ kind, double& hsum,
+                                                double& nmask) {
+  double pi[CH][4];
+  Tc mk[CH][4];
+  double h = 0.0;
+  int nin = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double v = y[c][k], av = fabs(v);
+      const bool in = av <= r;
+      pi[c][k] = in ? v : copysign(r, v);
+      h += in ? 0.5 * v * v : r * av - 0.5 * r * r;
+      const bool real = 4 * (c * LANES + lane) + k < d;
+      mk[c][k] = (in && real) ? (Tc)1 : (Tc)0;
+      nin += (in && real) ? 1 : 0;
+    }
+  h = group_sum<LANES>(h, mask);
+  nin = (int)group_sum<LANES>((double)nin, mask);
+  uint8_t kd;
+  if (!(r > 0.0)) kd = K_INERT;
+  else if (nin == d) kd = K_IN;
+  else kd = K_MASK;
+  if (lane == 0) {
+    hsum += h;
+    nmask += kd == K_MASK ? 1.0 : 0.0;
+    kind[e] = kd;
+    alpha[e] = (Tc)((double)nin / (double)d);
+  }
+  row_store<LANES, CH>(Ut + e * ld, ld, lane, pi);
+  if (kd == K_MASK) row_store<LANES, CH>(Yh + e * ld, ld, lane, mk);
+}
+
+template <int LANES, int CH, typename Tc>
+__global__ void __launch_bounds__(256)
+k_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
+               const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
+               double sigma, double* __restrict__ Ut, Tc* __restrict__ Yh, Tc* __restrict__ alpha,
+               uint8_t* __restrict__ kind, int64_t m, int d, int ld, double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t e = g0; e < m; e += ng) {
+    const int2 ij = edges[e];
+    const double r = gamma * w[e];
+    double xi[CH][4], xj[CH][4], y[CH][4];
+    row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, xi);
+    row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, xj);
+    row_load<LANES, CH>(U + e * ld, ld, lane, y);
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) y[c][k] = fma(sigma, xi[c][k] - xj[c][k], y[c][k]);
+    q1_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[0],
+                                   acc[1]);
+  }
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_E], tot) && threadIdx.x == 0) {
+    ctl->eval[0] = tot[0];
+    ctl->eval[3] = tot[1];
+  }
+}
+
+// KKT (q = 1) fused with the next evaluation: primal residual bx - soft(bx + u, r)
+// (soft threshold = prox of r ||.||_1), r ||bx||_1 for f_p, then the edge outputs.
+template <int LANES, int CH, typename Tc>
+__global__ void __launch_bounds__(256)
+k_kkt_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
+                   const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
+                   double sigma, double* __restrict__ Ut, Tc* __restrict__ Yh,
+                   Tc* __restrict__ alpha, uint8_t* __restrict__ kind, int64_t m, int d, int ld,
+                   double* partials, Ctl* ctl) {
+  const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // ||res||^2, sum r||bx||_1, sum h, #mask edges
+  for (int64_t e = g0; e < m; e += ng) {
+    const int2 ij = edges[e];
+    const double r = gamma * w[e];
+    double bx[CH][4], u[CH][4], y[CH][4];
+    row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, bx);
+    row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, y);
+    row_load<LANES, CH>(U + e * ld, ld, lane, u);
+    double sres = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        bx[c][k] -= y[c][k];
+        s1 += fabs(bx[c][k]);
+        const double v = u[c][k] + bx[c][k];
+        const double soft = copysign(fmax(fabs(v) - r, 0.0), v);
+        const double res = bx[c][k] - soft;
+        sres = fma(res, res, sres);
+        y[c][k] = fma(sigma, bx[c][k], u[c][k]);
+      }
+    s1 = group_sum<LANES>(s1, mask);
+    acc[0] += sres;
+    if (lane == 0) acc[1] += r * s1;
+    q1_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[2],
+                                   acc[3]);
   }
   double tot[4];
   if (grid_reduce<4>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {

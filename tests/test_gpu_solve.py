@@ -94,7 +94,7 @@ def test_rejects_bad_input(ccm):
     edges, w, _ = ograph.build_graph(A, 4, 0.5)
     At, Et, wt = _to_dev(A, edges, w)
     with pytest.raises(ccm.CCMError):
-        ccm.solve_path(At, Et, wt, [0.1], q=1)
+        ccm.solve_path(At, Et, wt, [0.1], q=3)           # q = 1 and 2 only
     bad = edges.copy()
     bad[3] = [5, 5]
     with pytest.raises(ccm.CCMError):
