@@ -1,4 +1,4 @@
-"""Model CCM (q = 2 or q = 1) by ADMM (oracle cross-check).
+"""Model CCM (q = 2, 1 or inf) by ADMM (oracle cross-check).
 
 ADMM is one of the three solvers the paper's package offers (Sec. 1, Table 1,
 Table 3). Here it is a second, independent route to the unique minimiser X*,
@@ -18,7 +18,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .kkt import incidence, kkt, prox_group, prox_l1
+from .kkt import incidence, kkt, prox_group, prox_l1, prox_linf
 
 __all__ = ["solve"]
 
@@ -39,7 +39,8 @@ def solve(A, edges, w, gamma, sigma=1.0, tol=1e-10, max_iter=200000, check_every
         rhs = A + B.T @ (sigma * Z - U)
         X = np.column_stack([solve_x(rhs[:, c]) for c in range(d)])
         BX = B @ X
-        Z = (prox_l1 if q == 1 else prox_group)(BX + U / sigma, r / sigma)
+        prox = prox_l1 if q == 1 else (prox_linf if q == np.inf else prox_group)
+        Z = prox(BX + U / sigma, r / sigma)
         U = U + sigma * (BX - Z)
         if it % check_every == 0:
             res = kkt(A, edges, w, gamma, X, U, q)

@@ -1,4 +1,4 @@
-"""Optimality measures for model CCM with q = 2 or q = 1 (oracle).
+"""Optimality measures for model CCM with q = 2, q = 1 or q = inf (oracle).
 
 Notation. For edges l = (i, j), i < j: (BX)_l = x_i - x_j; r_l = gamma * w_l;
 p(Z) = sum_l r_l ||z_l||_2. The primal is min_X 1/2||X - A||^2 + p(BX) (model
@@ -13,7 +13,11 @@ Readings (the paper gives only the gap of Sec. 4):
 * kkt   = max(eta_D, eta_P)
 
 For q = 1 the penalty is p(Z) = sum_l r_l ||z_l||_1, the dual ball is
-||u_l||_inf <= r_l and prox_p is the elementwise soft threshold.
+||u_l||_inf <= r_l and prox_p is the elementwise soft threshold. For q = inf
+(passed as numpy.inf) the penalty is sum_l r_l ||z_l||_inf, the dual ball is
+||u_l||_1 <= r_l and prox_p = I - (projection onto that ball) by the Moreau
+decomposition; the projection follows the sort-and-threshold method of Duchi,
+Shalev-Shwartz, Singer and Chandra (ICML 2008).
 
 Pinned by: weak duality (gap >= 0 whenever U is feasible), exact zeros at the
 closed-form n = 2 solution and at gamma = 0, and agreement of two independent
@@ -24,7 +28,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["incidence", "prox_group", "prox_l1", "kkt"]
+__all__ = ["incidence", "prox_group", "prox_l1", "proj_l1ball", "prox_linf", "kkt"]
 
 
 def incidence(edges: np.ndarray, n: int) -> sp.csr_matrix:
@@ -50,6 +54,41 @@ def prox_l1(V: np.ndarray, r: np.ndarray) -> np.ndarray:
     return np.sign(V) * np.maximum(np.abs(V) - r[:, None], 0.0)
 
 
+def proj_l1ball(V: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """Row-wise Euclidean projection of V onto {u : ||u||_1 <= r_l}.
+
+    Rows already inside (||v||_1 <= r_l) are returned unchanged. Otherwise the
+    magnitudes are sorted in decreasing order (mu_1 >= mu_2 >= ...), rho is the
+    largest j with mu_j > (mu_1 + ... + mu_j - r_l) / j, and the result is the
+    soft threshold of the row at theta = (mu_1 + ... + mu_rho - r_l) / rho.
+    Pinned by the variational inequality at the ball's vertices and by d = 1
+    (tests/test_oracle_solvers.py).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    out = V.copy()
+    for l in range(V.shape[0]):
+        v = V[l]
+        av = np.abs(v)
+        if np.sum(av) <= r[l]:
+            continue
+        if r[l] <= 0.0:
+            out[l] = 0.0
+            continue
+        mu = np.sort(av)[::-1]
+        cs = np.cumsum(mu)
+        j = np.arange(1, mu.size + 1)
+        rho = int(np.nonzero(mu * j > cs - r[l])[0][-1]) + 1
+        theta = (cs[rho - 1] - r[l]) / rho
+        out[l] = np.sign(v) * np.maximum(av - theta, 0.0)
+    return out
+
+
+def prox_linf(V: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """Row-wise prox of r_l ||.||_inf (Moreau: v - projection onto the l1 ball)."""
+    return np.asarray(V, dtype=np.float64) - proj_l1ball(V, r)
+
+
 def kkt(A, edges, w, gamma, X, U, q=2):
     """Residuals and objectives at (X, U); returns a dict."""
     A = np.asarray(A, dtype=np.float64)
@@ -64,6 +103,10 @@ def kkt(A, edges, w, gamma, X, U, q=2):
         eta_p = np.linalg.norm(BX - prox_l1(BX + U, r)) / (1.0 + nA)
         pen = np.sum(r * np.sum(np.abs(BX), axis=1))
         nu = np.max(np.abs(U), axis=1) if U.size else np.zeros(0)
+    elif q == np.inf:
+        eta_p = np.linalg.norm(BX - prox_linf(BX + U, r)) / (1.0 + nA)
+        pen = np.sum(r * np.max(np.abs(BX), axis=1)) if BX.size else 0.0
+        nu = np.sum(np.abs(U), axis=1)
     else:
         eta_p = np.linalg.norm(BX - prox_group(BX + U, r)) / (1.0 + nA)
         pen = np.sum(r * np.sqrt(np.sum(BX * BX, axis=1)))

@@ -1,4 +1,4 @@
-"""Model CCM (q = 2) along a gamma path by a textbook SSNAL (oracle).
+"""Model CCM (q = 2, 1 or inf) along a gamma path by a textbook SSNAL (oracle).
 
 Sec. 1 states the model and names SSNAL (semismooth Newton augmented
 Lagrangian) as the second-order solver; the paper prints none of its steps.
@@ -30,7 +30,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .kkt import incidence, kkt
+from .kkt import incidence, kkt, proj_l1ball
 
 __all__ = ["solve", "solve_path"]
 
@@ -40,8 +40,18 @@ def _eval(X, A, U, B, r, sigma, q=2):
 
     For q = 1 the ball is ||u_l||_inf <= r_l: Pi clamps each element to
     [-r_l, r_l], h is the elementwise Huber function, and the last return is |y|.
+    For q = inf the ball is ||u_l||_1 <= r_l, Pi is the l1-ball projection,
+    h(y) = (||y||^2 - ||y - Pi(y)||^2) / 2 (the Moreau envelope identity that also
+    gives the q = 2 and q = 1 forms), and the last return is Pi(y).
     """
     Y = U + sigma * (B @ X)
+    if q == np.inf:
+        PiY = proj_l1ball(Y, r)
+        D = Y - PiY
+        h = 0.5 * (np.sum(Y * Y, axis=1) - np.sum(D * D, axis=1))
+        phi = 0.5 * np.sum((X - A) ** 2) + np.sum(h) / sigma
+        G = X - A + B.T @ PiY
+        return phi, G, PiY, Y, PiY
     if q == 1:
         ay = np.abs(Y)
         rr = r[:, None]
@@ -68,6 +78,27 @@ def _mask_l1(ay, r):
     return ((ay <= r[:, None]) & (r[:, None] > 0)).astype(np.float64)
 
 
+def _linf_parts(Y, PiY, r):
+    """q = inf: P_l = diag(mask_l) - s_l s_l^T (an element of the generalized
+    Jacobian of the l1-ball projection). Inside rows (||y_l||_1 <= r_l, r_l > 0):
+    mask = 1, s = 0 (P = I). Outside rows: mask = 1 on the support S of Pi(y_l)
+    and s = sign(y_l) mask / sqrt(|S|). r_l = 0: mask = 0 (P = 0)."""
+    m, d = Y.shape
+    mask = np.zeros((m, d))
+    svec = np.zeros((m, d))
+    l1 = np.sum(np.abs(Y), axis=1)
+    for l in range(m):
+        if r[l] <= 0.0:
+            continue
+        if l1[l] <= r[l]:
+            mask[l] = 1.0
+            continue
+        S = PiY[l] != 0.0
+        mask[l, S] = 1.0
+        svec[l, S] = np.sign(Y[l, S]) / np.sqrt(np.count_nonzero(S))
+    return mask, svec
+
+
 def _jacobian_parts(Y, ny, r):
     """alpha_l and yhat_l of P_l = alpha_l (I - yhat yhat^T), or identity rows."""
     inside = (ny <= r) & (r > 0)
@@ -80,8 +111,11 @@ def _jacobian_parts(Y, ny, r):
     return alpha, yhat
 
 
-def _apply_V(Dv, B, alpha, yhat, sigma, mask=None):
+def _apply_V(Dv, B, alpha, yhat, sigma, mask=None, svec=None):
     BD = B @ Dv
+    if svec is not None:
+        s = np.sum(svec * BD, axis=1)
+        return Dv + sigma * (B.T @ (mask * BD - s[:, None] * svec))
     if mask is not None:
         return Dv + sigma * (B.T @ (mask * BD))
     s = np.sum(yhat * BD, axis=1)
@@ -89,10 +123,12 @@ def _apply_V(Dv, B, alpha, yhat, sigma, mask=None):
     return Dv + sigma * (B.T @ PBD)
 
 
-def _dense_V(n, d, edges, alpha, yhat, sigma, mask=None):
+def _dense_V(n, d, edges, alpha, yhat, sigma, mask=None, svec=None):
     V = np.eye(n * d)
     for l in range(edges.shape[0]):
-        if mask is not None:
+        if svec is not None:
+            P = np.diag(mask[l]) - np.outer(svec[l], svec[l])
+        elif mask is not None:
             P = np.diag(mask[l])
         elif alpha[l] == 0.0:
             continue
@@ -107,13 +143,15 @@ def _dense_V(n, d, edges, alpha, yhat, sigma, mask=None):
     return V
 
 
-def _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method, cg_rtol, mask=None):
+def _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method, cg_rtol, mask=None,
+                      svec=None):
     if method == "dense":
-        V = _dense_V(n, d, edges, alpha, yhat, sigma, mask)
+        V = _dense_V(n, d, edges, alpha, yhat, sigma, mask, svec)
         return np.linalg.solve(V, -G.reshape(-1)).reshape(n, d), 0
     op = spla.LinearOperator(
         (n * d, n * d),
-        matvec=lambda v: _apply_V(v.reshape(n, d), B, alpha, yhat, sigma, mask).reshape(-1),
+        matvec=lambda v: _apply_V(v.reshape(n, d), B, alpha, yhat, sigma, mask,
+                                  svec).reshape(-1),
         dtype=np.float64)
     it = [0]
 
@@ -127,7 +165,7 @@ def _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method, cg_rtol, ma
 
 def solve(A, edges, w, gamma, X0=None, U0=None, sigma0=1.0, tol=1e-11,
           max_outer=300, max_newton=60, method=None, sigma_max=1e4, q=2):
-    """Solve model CCM (q = 2 or q = 1) at one gamma. Returns (X, U, sigma, info)."""
+    """Solve model CCM (q = 2, 1 or inf) at one gamma. Returns (X, U, sigma, info)."""
     A = np.asarray(A, dtype=np.float64)
     edges = np.asarray(edges, dtype=np.int64)
     n, d = A.shape
@@ -153,16 +191,19 @@ def solve(A, edges, w, gamma, X0=None, U0=None, sigma0=1.0, tol=1e-11,
         for _ in range(max_newton):
             if np.linalg.norm(G) / (1.0 + nA) <= eps_in:
                 break
-            mask = None
+            mask = svec = None
             if q == 1:
                 mask = _mask_l1(ny, r)
+                alpha = yhat = None
+            elif q == np.inf:
+                mask, svec = _linf_parts(Y, ny, r)
                 alpha = yhat = None
             else:
                 alpha, yhat = _jacobian_parts(Y, ny, r)
             gn = np.linalg.norm(G)
             cg_rtol = max(1e-14, min(1e-3, 1e-2 * gn / (1.0 + nA)))
             Dv, cgit = _newton_direction(G, B, edges, alpha, yhat, sigma, n, d, method,
-                                         cg_rtol, mask)
+                                         cg_rtol, mask, svec)
             info["cg"] += cgit
             gd = float(np.sum(G * Dv))
             t = 1.0

@@ -225,3 +225,135 @@ def test_weak_duality_q1():
         res = kkt.kkt(A, edges, w, g, X, U, q=1)
         assert res["fd"] <= res["fp"] + 1e-12
         assert res["dual_infeas"] == 0.0
+
+
+# ---------------------------------------------------------------- q = inf
+def _vi_violation(v, u, r):
+    """Largest <v - u, e - u> over the 2d vertices e = +-r e_k of the l1 ball.
+
+    u is the projection of v onto the ball iff u is in the ball and this is <= 0
+    (the ball is the convex hull of its vertices, so checking the variational
+    inequality at the vertices checks it everywhere)."""
+    g = v - u
+    worst = -np.inf
+    for k in range(v.size):
+        for sgn in (1.0, -1.0):
+            e = np.zeros_like(v)
+            e[k] = sgn * r
+            worst = max(worst, float(g @ (e - u)))
+    return worst
+
+
+def test_l1ball_projection_variational_inequality():
+    rng = np.random.default_rng(21)
+    for trial in range(300):
+        d = int(rng.integers(1, 13))
+        v = rng.normal(size=d) * rng.choice([0.1, 1.0, 10.0])
+        if trial % 5 == 0:   # ties and zeros
+            v = np.round(v) + 0.0
+        r = float(rng.uniform(0.0, 1.5) * max(np.sum(np.abs(v)), 1e-3))
+        u = kkt.proj_l1ball(v[None, :], np.array([r]))[0]
+        scale = 1.0 + np.sum(np.abs(v)) ** 2
+        assert np.sum(np.abs(u)) <= r * (1 + 1e-12) + 1e-15
+        if np.sum(np.abs(v)) <= r:
+            assert np.array_equal(u, v)
+        else:
+            assert _vi_violation(v, u, r) <= 1e-12 * scale
+
+
+def test_l1ball_vi_catches_planted_threshold_error():
+    """A plausible mistake (dividing by rho + 1 instead of rho) fails the pin above."""
+    v = np.array([3.0, -1.0, 0.5, 2.0])
+    r = 2.0
+    mu = np.sort(np.abs(v))[::-1]
+    cs = np.cumsum(mu)
+    j = np.arange(1, 5)
+    rho = int(np.nonzero(mu * j > cs - r)[0][-1]) + 1
+    bad = np.sign(v) * np.maximum(np.abs(v) - (cs[rho - 1] - r) / (rho + 1), 0.0)
+    assert _vi_violation(v, bad, r) > 1e-6 or np.sum(np.abs(bad)) > r * (1 + 1e-9)
+
+
+def test_linf_prox_and_projection_at_d1():
+    """d = 1: the l1 ball is [-r, r] and prox of r|.| is the soft threshold."""
+    v = np.array([[-3.0], [-0.2], [0.0], [0.7], [5.0]])
+    r = np.array([1.0, 1.0, 0.5, 0.5, 2.0])
+    np.testing.assert_array_equal(kkt.proj_l1ball(v, r)[:, 0], np.clip(v[:, 0], -r, r))
+    np.testing.assert_array_equal(kkt.prox_linf(v, r)[:, 0],
+                                  np.sign(v[:, 0]) * np.maximum(np.abs(v[:, 0]) - r, 0.0))
+
+
+def test_linf_jacobian_matches_finite_differences():
+    """diag(mask) - s s^T (the oracle's P_l for q = inf) is the derivative of the
+    l1-ball projection away from its kinks."""
+    rng = np.random.default_rng(22)
+    for _ in range(40):
+        d = int(rng.integers(2, 9))
+        y = rng.normal(size=d) * 2.0
+        r = float(rng.uniform(0.2, 1.2) * np.sum(np.abs(y)))
+        pi = kkt.proj_l1ball(y[None, :], np.array([r]))
+        mask, svec = ssnal._linf_parts(y[None, :], pi, np.array([r]))
+        P = np.diag(mask[0]) - np.outer(svec[0], svec[0])
+        h = 1e-7
+        J = np.zeros((d, d))
+        for k in range(d):
+            e = np.zeros(d)
+            e[k] = h
+            J[:, k] = (kkt.proj_l1ball((y + e)[None, :], np.array([r]))[0]
+                       - kkt.proj_l1ball((y - e)[None, :], np.array([r]))[0]) / (2 * h)
+        np.testing.assert_allclose(P, J, atol=1e-6)
+
+
+def test_two_points_closed_form_qinf():
+    """n = 2, q = inf, w = 1, a1 - a2 = (4, 1): the penalty r||x1 - x2||_inf first
+    shrinks only the larger coordinate of the difference (by 2r) until the two
+    coordinates are equal (2r = 3), then both together, and the points fuse at
+    2r = ||a1 - a2||_1 = 5. Differences by hand: gamma = 1 -> (2, 1),
+    gamma = 2 -> (0.5, 0.5), gamma = 3 -> (0, 0); the mean (3, 0.5) stays."""
+    a = np.array([[5.0, 1.0], [1.0, 0.0]])
+    E = np.array([[0, 1]])
+    w = np.array([1.0])
+    mid = np.array([3.0, 0.5])
+    for gamma, z in [(1.0, (2.0, 1.0)), (2.0, (0.5, 0.5)), (3.0, (0.0, 0.0))]:
+        z = np.array(z)
+        X, U, _, info = ssnal.solve(a, E, w, gamma, tol=1e-13, q=np.inf)
+        np.testing.assert_allclose(X, np.stack([mid + z / 2, mid - z / 2]), atol=1e-11)
+        assert info["kkt"] <= 1e-12
+        assert kkt.kkt(a, E, w, gamma, X, U, q=np.inf)["dual_infeas"] <= 1e-12
+    # the same with the larger coordinate negative and in second place
+    b = np.array([[1.0, -3.0], [0.0, 1.0]])           # a1 - a2 = (1, -4)
+    X, _, _, _ = ssnal.solve(b, E, w, 1.0, tol=1e-13, q=np.inf)
+    np.testing.assert_allclose(X[0] - X[1], [1.0, -2.0], atol=1e-11)
+
+
+@pytest.mark.parametrize("gamma", [0.01, 0.05, 0.3])
+def test_qinf_in_one_dimension_is_the_exact_1d_path(gamma):
+    """d = 1: every q-norm is |.|, so q = inf reduces to the certified exact 1-D path."""
+    a = np.random.default_rng(23).normal(size=(14, 1))
+    E = exact1d.complete_graph(14)
+    w = np.ones(E.shape[0])
+    X, _, _, info = ssnal.solve(a, E, w, gamma, tol=1e-12, q=np.inf)
+    np.testing.assert_allclose(X[:, 0], exact1d.solve(a[:, 0], gamma), atol=1e-10)
+
+
+def test_ssnal_matches_admm_qinf():
+    A, edges, w = _small_problem(seed=24, n=30, d=3, k=5)
+    for g in [0.05, 0.4, 2.0]:
+        X, _, _, info = ssnal.solve(A, edges, w, g, tol=1e-12, q=np.inf)
+        Xa, _, ra = admm.solve(A, edges, w, g, tol=1e-11, max_iter=50000, q=np.inf)
+        assert info["kkt"] <= 1e-11
+        np.testing.assert_allclose(X, Xa, atol=1e-8)
+
+
+def test_weak_duality_qinf():
+    """f_d(U) <= f_p(X) for every X and every U with ||u_l||_1 <= r_l."""
+    A, edges, w = _small_problem(seed=25, n=25, d=3, k=4)
+    rng = np.random.default_rng(26)
+    g = 0.4
+    r = g * w
+    for _ in range(20):
+        X = A + rng.normal(size=A.shape)
+        U = rng.normal(size=(edges.shape[0], 3))
+        U *= (rng.uniform(0, 1, size=edges.shape[0]) * r / np.sum(np.abs(U), axis=1))[:, None]
+        res = kkt.kkt(A, edges, w, g, X, U, q=np.inf)
+        assert res["fd"] <= res["fp"] + 1e-12
+        assert res["dual_infeas"] == 0.0
