@@ -95,14 +95,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_problem(seed):
-    A, _, wl = synth.make_workload(WORKLOAD, seed)
+def make_problem(seed, workload=WORKLOAD):
+    A, _, wl = synth.make_workload(workload, seed)
     gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
     return A, wl, gam
 
 
 def run_oracle_sample(seed, budget_s=15.0):
-    """CPU oracle on a bounded sample: the same recipe at n = 600 points, the
+    """CPU oracle on a bounded sample: the same recipe at n = 300 points, the
     full gamma grid; returns (gamma-solves/s, description)."""
     import contextlib
     try:
@@ -292,31 +292,38 @@ def form_admm(args):
     return 0
 
 
-def form_q1(args):
-    """Model CCM with q = 1 (l1 norm on x_i - x_j) against q = 2 on the bench
-    workload: graph build + path, same tolerance, device-resident."""
+def form_qnorm(args):
+    """Model CCM with q = 1 (l1 norm on x_i - x_j) and q = inf (max norm) against
+    q = 2 on the bench workload: graph build + path, same tolerance,
+    device-resident."""
     import torch
     import paper_2501_15964_b300 as ccm
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    A, wl, gam = make_problem(0)
+    A, wl, gam = make_problem(0, args.workload)
     if args.n_gamma > 0:
         gam = gam[: args.n_gamma]
     At = torch.tensor(A, device="cuda")
     out = {}
-    for q in (2, 1):
+    for q in args.qs.split(","):
         def step():
             E, w, _ = ccm.build_graph(At, wl.k, wl.phi)
             return ccm.solve_path(At, E, w, gam, q=q, tol=SOLVE_TOL)
-        step()
+        if args.warmup > 0:
+            step()
         ms, (_, _, _, st) = _time(step, stream, args.steps)
         out[f"q{q}"] = {"value": len(gam) / (ms / 1000.0), "ms": ms,
                         "newton": sum(s["newton"] for s in st), "cg": sum(s["cg"] for s in st),
                         "max_kkt": max(s["kkt"] for s in st), "max_gap": max(s["gap"] for s in st),
                         "not_converged": sum(1 for s in st if s["status"] != 0),
-                        "clusters_last_gamma": st[-1]["n_clusters"]}
-    line = {"form": "q1", "metric": "gamma-solves/s, q = 1 vs q = 2 (graph build + path)",
-            "unit": "gamma-solves/s", "workload": WORKLOAD, "gammas": len(gam), "tol": SOLVE_TOL,
+                        "clusters_last_gamma": st[-1]["n_clusters"],
+                        "newton_per_gamma": [s["newton"] for s in st],
+                        "cg_per_gamma": [s["cg"] for s in st]}
+        print(json.dumps({"form": "qnorm", "workload": args.workload, "q": q, **out[f"q{q}"]}),
+              flush=True)
+    line = {"form": "qnorm", "metric": "gamma-solves/s for q = " + args.qs + " (graph build + path)",
+            "unit": "gamma-solves/s", "workload": args.workload, "gammas": len(gam),
+            "tol": SOLVE_TOL,
             **out}
     print(json.dumps(line), flush=True)
     return 0
@@ -334,12 +341,14 @@ def main():
                     help="synthetic workload (default: the MNIST-shaped one)")
     ap.add_argument("--n-gamma", type=int, default=0,
                     help="solve only the first N gammas of the path (profiling runs)")
+    ap.add_argument("--qs", default="2,1,inf",
+                    help="comma-separated q values of the qnorm form (1, 2, inf)")
     ap.add_argument("--gamma-from", type=int, default=0,
                     help="start the path at this index of the gamma grid, cold (profiling runs)")
     ap.add_argument("--form", default="path",
-                    choices=["path", "batched", "adjoint", "admm", "q1"],
+                    choices=["path", "batched", "adjoint", "admm", "qnorm"],
                     help="path (default, the JSON contract line), or the batched, adjoint, "
-                         "ADMM / fast AMA or q = 1 comparison")
+                         "ADMM / fast AMA or q-norm (q = 2, 1, inf) comparison")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched form")
     ap.add_argument("--loop", type=int, default=32,
                     help="problems solved one by one for the batched comparison")
@@ -351,8 +360,8 @@ def main():
         return form_vjp(args)
     if args.form == "admm":
         return form_admm(args)
-    if args.form == "q1":
-        return form_q1(args)
+    if args.form == "qnorm":
+        return form_qnorm(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

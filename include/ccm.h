@@ -37,13 +37,16 @@ typedef struct ccm_ctx ccm_ctx;
 typedef enum {
   CCM_OK = 0,
   CCM_ERR_INVALID_ARG = 1,      /* bad size, pointer, or value; nothing was launched */
-  CCM_ERR_UNSUPPORTED = 2,      /* e.g. q != 2, d above the compiled maximum */
+  CCM_ERR_UNSUPPORTED = 2,      /* e.g. q not 1, 2 or CCM_Q_INF; d above the compiled maximum */
   CCM_ERR_CUDA = 3,             /* a CUDA runtime call failed */
   CCM_ERR_OOM = 4,              /* scratch allocation failed */
   CCM_ERR_NOT_CONVERGED = 5,    /* an iteration cap was hit; outputs are still written */
   CCM_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
   CCM_ERR_BUFFER_TOO_SMALL = 7  /* an output capacity is too small; *m_out says how much */
 } ccm_status;
+
+/* The value of the int32 argument q that selects q = inf (the max norm). */
+#define CCM_Q_INF 2147483647
 
 typedef enum { CCM_PREC_FP64 = 0, CCM_PREC_MIXED = 1 } ccm_precision;
 typedef enum { CCM_ENGINE_AUTO = 0, CCM_ENGINE_GRID = 1, CCM_ENGINE_BLOCK = 2 } ccm_engine;
@@ -134,15 +137,20 @@ int ccm_build_graph(ccm_ctx* ctx, const double* A, int64_t n, int32_t d, int32_t
  *
  * A: n x d; edges: m x 2 (see conventions); w: m float64 >= 0;
  * gammas: HOST array of T non-decreasing values >= 0; q = 2 (the Euclidean norm
- * of x_i - x_j) or q = 1 (its l1 norm: the dual ball becomes ||u_l||_inf <= r_l,
- * the Newton Jacobian a 0/1 diagonal per edge; grid engine only), others
+ * of x_i - x_j), q = 1 (its l1 norm: the dual ball becomes ||u_l||_inf <= r_l,
+ * the Newton Jacobian a 0/1 diagonal per edge) or q = CCM_Q_INF (its max norm:
+ * the dual ball becomes ||u_l||_1 <= r_l, projected onto by an active-set
+ * threshold search per edge, the Jacobian diag(mask) - s s^T on the support of
+ * the projection); q = 1 and q = inf run on the grid engine only; other q give
  * CCM_ERR_UNSUPPORTED; tol > 0: stop each gamma when max(eta_d, eta_p) <= tol
  * and the relative duality gap of Sec. 4 is <= tol (definitions in ccm_stats).
  * Outputs: X: T x n x d float64; labels: T x n int32 or NULL (label = rank of the
  * cluster's smallest node index; an edge is fused when the float64 squared
  * distance of its endpoints, summed in feature order without FMA, is <= 1e-12);
  * U: T x m x d float64 or NULL (final multipliers); stats: HOST array of T or NULL.
- * For q = 1, eta_p uses prox of r_l ||.||_1 (soft threshold) and f_p r_l ||.||_1.
+ * For q = 1, eta_p uses prox of r_l ||.||_1 (soft threshold) and f_p r_l ||.||_1;
+ * for q = inf, prox of r_l ||.||_inf (identity minus the l1-ball projection) and
+ * r_l ||.||_inf.
  * Returns CCM_ERR_NOT_CONVERGED if any gamma hit an iteration cap (all outputs
  * are still written; stats[t].status says which).
  */

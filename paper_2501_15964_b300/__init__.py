@@ -1,4 +1,4 @@
-"""Convex clustering (model CCM, q = 2) along a gamma path on one B300.
+"""Convex clustering (model CCM; q = 2, 1 or inf) along a gamma path on one B300.
 
 Thin Python binding of ``libccm.so`` (C ABI declared in ``include/ccm.h``).
 Every computation runs in the library's CUDA kernels; this module only
@@ -15,6 +15,7 @@ from ._lib import (  # noqa: F401
     Context,
     Options,
     PREC_FP64,
+    Q_INF,
     PREC_MIXED,
     ENGINE_AUTO,
     ENGINE_BLOCK,

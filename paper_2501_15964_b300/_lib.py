@@ -5,6 +5,7 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+Q_INF = 2147483647  # CCM_Q_INF: the int32 q that selects the max norm
 _LIB = None
 
 PREC_FP64, PREC_MIXED = 0, 1

@@ -5,7 +5,8 @@ import ctypes as C
 
 import torch
 
-from ._lib import (CCMError, Context, Options, Problem, Profile, Stats, check, load_library)
+from ._lib import (Q_INF, CCMError, Context, Options, Problem, Profile, Stats, check,
+                   load_library)
 
 _CTX: dict[int, Context] = {}
 
@@ -29,6 +30,15 @@ def _dev(t: torch.Tensor, dtype, name):
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     return t.contiguous()
+
+
+def _q_arg(q) -> int:
+    """The int32 q of the C ABI: 1, 2, or Q_INF for q = inf (math.inf or "inf")."""
+    if isinstance(q, str) and q.lower() in ("inf", "infinity"):
+        return Q_INF
+    if isinstance(q, float) and q == float("inf"):
+        return Q_INF
+    return int(q)
 
 
 def _ptr(t):
@@ -86,7 +96,7 @@ def solve_path(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U: boo
     garr = (C.c_double * T)(*g)
     opt = make_options(**options)
     st = load_library().ccm_solve_path(ctx.handle, _ptr(A), n, d, _ptr(edges), _ptr(w), m, garr,
-                                       T, int(q), float(tol), C.byref(opt), _ptr(X), _ptr(lab),
+                                       T, _q_arg(q), float(tol), C.byref(opt), _ptr(X), _ptr(lab),
                                        _ptr(U), stats, _stream())
     if st != 0 and not (st == 5 and not raise_on_cap):
         check(st)
@@ -126,7 +136,7 @@ def _solve_path_with(entry, A, edges, w, gammas, tol, q, return_U, labels_out, c
     garr = (C.c_double * T)(*g)
     opt = make_options(**options)
     st = getattr(load_library(), entry)(ctx.handle, _ptr(A), n, d, _ptr(edges), _ptr(w), m, garr,
-                                        T, int(q), float(tol), C.byref(opt), _ptr(X), _ptr(lab),
+                                        T, _q_arg(q), float(tol), C.byref(opt), _ptr(X), _ptr(lab),
                                         _ptr(U), stats, _stream())
     if st != 0 and not (st == 5 and not raise_on_cap):
         check(st)

@@ -150,7 +150,7 @@ k_cg_matvec_ring(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc
         if (mc != (Tc)0) {
           Tc* dst = ring + (size_t)pslot * 2 * ld;
           row_copy_async<LANES, CH>(dst, R + (int64_t)ey * ld, ld, lane, pol_keep);
-          if (mc < (Tc)0 || mc > (Tc)1.5)  // yhat row, or the q = 1 mask row
+          if (mc < (Tc)0 || mc > (Tc)1.5)  // yhat row, the q = 1 mask row or the q = inf s row
             row_copy_async<LANES, CH>(dst + ld, Yh + (int64_t)ex * ld, ld, lane, pol_stream);
         }
         ++pk;
@@ -188,7 +188,22 @@ k_cg_matvec_ring(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc
           for (int c = 0; c < CH; ++c)
 #pragma unroll
             for (int k = 0; k < 4; ++k) v[c][k] = u[c][k] - mo * v[c][k];
-          if (mc > (Tc)1.5) {  // q = 1: diagonal mask
+          if (mc > (Tc)2.5) {  // q = inf: diag(s != 0) - s s^T
+            Tc sv[CH][4];
+            row_load<LANES, CH>(rr + ld, ld, lane, sv);
+            Tc s4[4] = {(Tc)0, (Tc)0, (Tc)0, (Tc)0};
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+              for (int k = 0; k < 4; ++k) s4[k] += sv[c][k] * v[c][k];
+            Tc s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+            s = group_sum<LANES>(s, 0xffffffffu);
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                accv[c][k] += (sv[c][k] != (Tc)0 ? v[c][k] : (Tc)0) - s * sv[c][k];
+          } else if (mc > (Tc)1.5) {  // q = 1: diagonal mask
             Tc mk[CH][4];
             row_load<LANES, CH>(rr + ld, ld, lane, mk);
 #pragma unroll
@@ -314,7 +329,7 @@ k_node_grad_ring(const double* __restrict__ X, const double* __restrict__ Ap,
         const uint8_t kd = kind[eo.x];
         t = kd == K_IN ? 1.0
             : (kd == K_OUT ? (double)alpha[eo.x] * tr_out
-                           : (kd == K_MASK ? (double)alpha[eo.x] : -1.0));
+                           : ((kd == K_MASK || kd == K_LINF) ? (double)alpha[eo.x] : -1.0));
       }
     };
     fetch(kb, c_eo, c_t);

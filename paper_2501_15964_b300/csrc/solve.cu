@@ -332,9 +332,11 @@ struct GridEngine {
     // evaluate phi, grad phi, Pi(y), yhat, alpha at Xc (one edge pass + one node pass)
     auto evaluate = [&](const double* Xc, double* phi, double* gn, double* nout) -> int {
       if (a.q == 1)
-        k_edge_eval_q1<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
-                                                             Ut, Yh, alpha, kind, m, d, ld, part,
-                                                             ctl);
+        k_edge_eval_qn<1, L, CH, Tc><<<b_edge, threads, 0, s>>>(
+            Xc, U, edges, a.w, gamma_cur, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
+      else if (a.q == kQInf)
+        k_edge_eval_qn<kQInf, L, CH, Tc><<<b_edge, threads, 0, s>>>(
+            Xc, U, edges, a.w, gamma_cur, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
       else
         k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
                                                           Ut, Yh, alpha, kind, m, ld, part, ctl);
@@ -437,9 +439,11 @@ struct GridEngine {
         std::swap(U, Ut);
         // KKT at (X, U) fused with the edge part of the next evaluation at (X, U)
         if (a.q == 1)
-          k_kkt_edge_eval_q1<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma,
-                                                                   Ut, Yh, alpha, kind, m, d, ld,
-                                                                   part, ctl);
+          k_kkt_edge_eval_qn<1, L, CH, Tc><<<b_edge, threads, 0, s>>>(
+              X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
+        else if (a.q == kQInf)
+          k_kkt_edge_eval_qn<kQInf, L, CH, Tc><<<b_edge, threads, 0, s>>>(
+              X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
         else
           k_kkt_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma,
                                                                 Ut, Yh, alpha, kind, m, ld, part,
@@ -543,8 +547,9 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     set_error("ccm_solve_path: invalid argument");
     return CCM_ERR_INVALID_ARG;
   }
-  if (q != 2 && q != 1) {
-    set_error("ccm_solve_path: q = 1 and q = 2 are implemented (got q = %d)", q);
+  if (q != 2 && q != 1 && q != CCM_Q_INF) {
+    set_error("ccm_solve_path: q = 1, q = 2 and q = inf (CCM_Q_INF) are implemented (got q = %d)",
+              q);
     return CCM_ERR_UNSUPPORTED;
   }
   if (d > ccm_max_dim()) {

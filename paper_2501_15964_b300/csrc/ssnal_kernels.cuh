@@ -22,7 +22,14 @@ namespace ccm {
 
 // K_MASK (q = 1 only): P_l = diag(mask) with mask_k = 1 where |y_k| <= r_l; the
 // mask row is stored in the yhat slot and alpha holds trace(P_l)/d.
-enum EdgeKind : uint8_t { K_INERT = 0, K_IN = 1, K_OUT = 2, K_MASK = 3 };
+// K_LINF (q = inf only, y_l outside the l1 ball): P_l = diag(mask) - s s^T with
+// mask the support S of Pi(y_l) and s = sign(y_l) mask / sqrt(|S|); the unit
+// vector s is stored in the yhat slot (mask = s != 0) and alpha holds
+// trace(P_l)/d = (|S| - 1)/d (0 when |S| = 1, where P_l = 0).
+enum EdgeKind : uint8_t { K_INERT = 0, K_IN = 1, K_OUT = 2, K_MASK = 3, K_LINF = 4 };
+
+// The int32 value of q that selects q = inf.
+constexpr int kQInf = CCM_Q_INF;
 
 // Device-resident scalars of one solve (one problem).
 struct CgCtl {
@@ -198,7 +205,7 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
         const uint8_t kd = kind[e];
         diag += kd == K_IN ? 1.0
                 : (kd == K_OUT ? (double)alpha[e] * tr_out
-                               : (kd == K_MASK ? (double)alpha[e] : 0.0));
+                               : ((kd == K_MASK || kd == K_LINF) ? (double)alpha[e] : 0.0));
       }
       Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
     }
@@ -223,8 +230,9 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
 
 // Per-incidence operator coefficients, packed once per Newton step: c = 1
 // (inside edge, P_l = I), c = -alpha_l (outside edge, P_l = alpha_l (I - yhat yhat^T)),
-// c = 2 (q = 1 mask edge, P_l = diag(mask row)), c = 0 (inert edge); mo = Minv of
-// the incidence's other endpoint.
+// c = 2 (q = 1 mask edge, P_l = diag(mask row)), c = 3 (q = inf edge outside the
+// l1 ball, P_l = diag(s != 0) - s s^T), c = 0 (inert edge, or a q = inf edge with
+// |S| = 1, where P_l = 0); mo = Minv of the incidence's other endpoint.
 template <typename Tc>
 struct alignas(2 * sizeof(Tc)) IncMeta {
   Tc c, mo;
@@ -255,7 +263,10 @@ k_cg_init(const double* __restrict__ G, const Tc* __restrict__ Minv, Tc* __restr
       const int2 eo = inc[t];
       const uint8_t kd = kind[eo.x];
       IncMeta<Tc> mm;
-      mm.c = kd == K_IN ? (Tc)1 : (kd == K_OUT ? -alpha[eo.x] : (kd == K_MASK ? (Tc)2 : (Tc)0));
+      mm.c = kd == K_IN ? (Tc)1
+             : (kd == K_OUT ? -alpha[eo.x]
+                : (kd == K_MASK ? (Tc)2
+                   : ((kd == K_LINF && alpha[eo.x] > (Tc)0) ? (Tc)3 : (Tc)0)));
       mm.mo = Minv[eo.y];
       meta[t] = mm;
     }
@@ -339,7 +350,21 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
       for (int c = 0; c < CH; ++c)
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[c][k] = u[c][k] - mm.mo * v[c][k];
-      if (mm.c > (Tc)1.5) {  // q = 1: diagonal mask
+      if (mm.c > (Tc)2.5) {  // q = inf: diag(s != 0) - s s^T
+        Tc sv[CH][4];
+        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, sv);
+        Tc s = (Tc)0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) s += sv[c][k] * v[c][k];
+        s = group_sum<LANES>(s, mask);
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            accv[c][k] += (sv[c][k] != (Tc)0 ? v[c][k] : (Tc)0) - s * sv[c][k];
+      } else if (mm.c > (Tc)1.5) {  // q = 1: diagonal mask
         Tc mk[CH][4];
         row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, mk);
 #pragma unroll
@@ -611,9 +636,123 @@ __device__ __forceinline__ void q1_edge_outputs(const double (&y)[CH][4], double
   if (kd == K_MASK) row_store<LANES, CH>(Yh + e * ld, ld, lane, mk);
 }
 
+// ------------------------------------------------------------ q = inf
+// Model CCM with the max norm on the differences (Sec. 1 allows any q >= 1): the
+// ball of the dual is ||u_l||_1 <= r_l. Outside it, Pi(v)_k = sign(v_k)
+// max(|v_k| - theta, 0) with theta > 0 fixed by sum_k max(|v_k| - theta, 0) = r_l.
+// h_l(y) = (||y||^2 - ||y - Pi(y)||^2)/2 (Moreau envelope; the same identity gives
+// the q = 2 and q = 1 forms of h), and prox of r_l||.||_inf = I - Pi.
+
+template <int LANES>
+__device__ __forceinline__ double group_max(double x, unsigned mask) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(mask, x, o, LANES));
+  return x;
+}
+
+// theta of the projection of the row v (d real elements, lanes of one group) onto
+// {||u||_1 <= r}, for ||v||_1 = l1 > r > 0. Active-set iteration of Michelot
+// (1986): theta = (sum over S of |v_k| - r)/|S|, then S <- {k : |v_k| > theta},
+// from S = all d elements. theta never decreases (kept so under rounding by the
+// max below), so S only shrinks and the loop ends within d + 1 passes. The
+// butterfly sums are bitwise identical on all lanes, so every lane ends with the
+// same theta and the same pass count.
+template <int LANES, int CH>
+__device__ __forceinline__ double l1ball_theta(const double (&v)[CH][4], double l1, double r,
+                                               int d, unsigned mask) {
+  double theta = (l1 - r) / (double)d;
+  int cnt = d;
+  for (int pass = 0; pass <= d; ++pass) {
+    double sum = 0.0;
+    int c = 0;
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double av = fabs(v[cc][k]);
+        if (av > theta) {
+          sum += av;
+          ++c;
+        }
+      }
+    sum = group_sum<LANES>(sum, mask);
+    c = group_sum<LANES>(c, mask);
+    if (c == cnt || c == 0) break;
+    cnt = c;
+    theta = fmax(theta, (sum - r) / (double)c);
+  }
+  return theta;
+}
+
+// Pi(y) -> Ut, kind, alpha and (kind K_LINF) the unit vector s -> Yh for one edge
+// row y; adds h_l to hsum and 1 to nout when y_l is outside the ball.
 template <int LANES, int CH, typename Tc>
+__device__ __forceinline__ void linf_edge_outputs(const double (&y)[CH][4], double r, int d,
+                                                  int lane, int ld, unsigned mask, int64_t e,
+                                                  double* __restrict__ Ut, Tc* __restrict__ Yh,
+                                                  Tc* __restrict__ alpha,
+                                                  uint8_t* __restrict__ kind, double& hsum,
+                                                  double& nout) {
+  double l1 = 0.0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) l1 += fabs(y[c][k]);
+  l1 = group_sum<LANES>(l1, mask);
+  uint8_t kd;
+  double theta = 0.0;
+  if (!(r > 0.0)) {
+    kd = K_INERT;
+  } else if (l1 <= r) {
+    kd = K_IN;
+  } else {
+    kd = K_LINF;
+    theta = l1ball_theta<LANES, CH>(y, l1, r, d, mask);
+  }
+  double pi[CH][4];
+  double h = 0.0;
+  int nsup = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double v = y[c][k];
+      double p;
+      if (kd == K_IN) p = v;
+      else if (kd == K_INERT) p = 0.0;
+      else p = copysign(fmax(fabs(v) - theta, 0.0), v);
+      pi[c][k] = p;
+      const double df = v - p;
+      h += v * v - df * df;
+      nsup += (p != 0.0) ? 1 : 0;
+    }
+  h = 0.5 * group_sum<LANES>(h, mask);
+  if (kd == K_LINF) nsup = group_sum<LANES>(nsup, mask);
+  if (lane == 0) {
+    hsum += h;
+    nout += kd == K_LINF ? 1.0 : 0.0;
+    kind[e] = kd;
+    alpha[e] = (Tc)(kd == K_LINF ? (double)max(nsup - 1, 0) / (double)d
+                                 : (kd == K_IN ? 1.0 : 0.0));
+  }
+  row_store<LANES, CH>(Ut + e * ld, ld, lane, pi);
+  if (kd == K_LINF) {
+    const Tc iv = (Tc)(nsup > 0 ? 1.0 / sqrt((double)nsup) : 0.0);
+    Tc sv[CH][4];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        sv[c][k] = pi[c][k] != 0.0 ? (__double2hiint(y[c][k]) < 0 ? -iv : iv) : (Tc)0;
+    row_store<LANES, CH>(Yh + e * ld, ld, lane, sv);
+  }
+}
+
+// Edge pass of the evaluation for the separable-ball norms: Q = 1 (elementwise
+// clamp) or Q = kQInf (l1-ball projection).
+template <int Q, int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
-k_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
+k_edge_eval_qn(const double* __restrict__ X, const double* __restrict__ U,
                const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
                double sigma, double* __restrict__ Ut, Tc* __restrict__ Yh, Tc* __restrict__ alpha,
                uint8_t* __restrict__ kind, int64_t m, int d, int ld, double* partials, Ctl* ctl) {
@@ -633,8 +772,12 @@ k_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
     for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) y[c][k] = fma(sigma, xi[c][k] - xj[c][k], y[c][k]);
-    q1_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[0],
-                                   acc[1]);
+    if constexpr (Q == 1)
+      q1_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[0],
+                                     acc[1]);
+    else
+      linf_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[0],
+                                       acc[1]);
   }
   double tot[2];
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_E], tot) && threadIdx.x == 0) {
@@ -643,11 +786,13 @@ k_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
   }
 }
 
-// KKT (q = 1) fused with the next evaluation: primal residual bx - soft(bx + u, r)
-// (soft threshold = prox of r ||.||_1), r ||bx||_1 for f_p, then the edge outputs.
-template <int LANES, int CH, typename Tc>
+// KKT for Q = 1 or Q = kQInf fused with the next evaluation: primal residual
+// bx - prox_p(bx + u) and r ||bx||_q for f_p, then the edge outputs. For q = 1 the
+// prox is the soft threshold at r; for q = inf, bx - prox_p(v) = Pi(v) - u with
+// v = u + bx (Moreau decomposition), and the penalty is r max_k |bx_k|.
+template <int Q, int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
-k_kkt_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
+k_kkt_edge_eval_qn(const double* __restrict__ X, const double* __restrict__ U,
                    const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
                    double sigma, double* __restrict__ Ut, Tc* __restrict__ Yh,
                    Tc* __restrict__ alpha, uint8_t* __restrict__ kind, int64_t m, int d, int ld,
@@ -656,7 +801,7 @@ k_kkt_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
   const unsigned mask = group_mask<LANES>();
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // ||res||^2, sum r||bx||_1, sum h, #mask edges
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // ||res||^2, sum r||bx||_q, sum h, #outside edges
   for (int64_t e = g0; e < m; e += ng) {
     const int2 ij = edges[e];
     const double r = gamma * w[e];
@@ -664,24 +809,56 @@ k_kkt_edge_eval_q1(const double* __restrict__ X, const double* __restrict__ U,
     row_load<LANES, CH>(X + (int64_t)ij.x * ld, ld, lane, bx);
     row_load<LANES, CH>(X + (int64_t)ij.y * ld, ld, lane, y);
     row_load<LANES, CH>(U + e * ld, ld, lane, u);
-    double sres = 0.0, s1 = 0.0;
+    double sres = 0.0, sq = 0.0;
+    if constexpr (Q == 1) {
 #pragma unroll
-    for (int c = 0; c < CH; ++c)
+      for (int c = 0; c < CH; ++c)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bx[c][k] -= y[c][k];
-        s1 += fabs(bx[c][k]);
-        const double v = u[c][k] + bx[c][k];
-        const double soft = copysign(fmax(fabs(v) - r, 0.0), v);
-        const double res = bx[c][k] - soft;
-        sres = fma(res, res, sres);
-        y[c][k] = fma(sigma, bx[c][k], u[c][k]);
-      }
-    s1 = group_sum<LANES>(s1, mask);
+        for (int k = 0; k < 4; ++k) {
+          bx[c][k] -= y[c][k];
+          sq += fabs(bx[c][k]);
+          const double v = u[c][k] + bx[c][k];
+          const double soft = copysign(fmax(fabs(v) - r, 0.0), v);
+          const double res = bx[c][k] - soft;
+          sres = fma(res, res, sres);
+          y[c][k] = fma(sigma, bx[c][k], u[c][k]);
+        }
+      sq = group_sum<LANES>(sq, mask);
+    } else {
+      double l1 = 0.0;
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double b = bx[c][k] - y[c][k];
+          sq = fmax(sq, fabs(b));
+          y[c][k] = fma(sigma, b, u[c][k]);
+          bx[c][k] = u[c][k] + b;  // bx now holds v = u + bx
+          l1 += fabs(bx[c][k]);
+        }
+      sq = group_max<LANES>(sq, mask);
+      l1 = group_sum<LANES>(l1, mask);
+      const bool outside = r > 0.0 && l1 > r;
+      const double theta = outside ? l1ball_theta<LANES, CH>(bx, l1, r, d, mask) : 0.0;
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double v = bx[c][k];
+          const double p = outside ? copysign(fmax(fabs(v) - theta, 0.0), v)
+                                   : (r > 0.0 ? v : 0.0);
+          const double res = p - u[c][k];
+          sres = fma(res, res, sres);
+        }
+    }
     acc[0] += sres;
-    if (lane == 0) acc[1] += r * s1;
-    q1_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[2],
-                                   acc[3]);
+    if (lane == 0) acc[1] += r * sq;
+    if constexpr (Q == 1)
+      q1_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[2],
+                                     acc[3]);
+    else
+      linf_edge_outputs<LANES, CH, Tc>(y, r, d, lane, ld, mask, e, Ut, Yh, alpha, kind, acc[2],
+                                       acc[3]);
   }
   double tot[4];
   if (grid_reduce<4>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {
