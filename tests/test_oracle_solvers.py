@@ -357,3 +357,41 @@ def test_weak_duality_qinf():
         res = kkt.kkt(A, edges, w, g, X, U, q=np.inf)
         assert res["fd"] <= res["fp"] + 1e-12
         assert res["dual_infeas"] == 0.0
+
+
+# ---------------------------------------------------------------- q = 1 and q = inf
+@pytest.mark.parametrize("q", [1, np.inf])
+def test_separable_norms_invariances(q):
+    """For q = 1 and q = inf: sum x = sum a, translation and scaling equivariance,
+    and equivariance under signed permutations of the coordinates (the symmetry
+    group of both norms; a general rotation is not one of them)."""
+    A, edges, w = _small_problem(seed=41, n=24, d=3, k=4)
+    g = 0.3
+    X, _, _, _ = ssnal.solve(A, edges, w, g, tol=1e-12, q=q)
+    np.testing.assert_allclose(X.sum(0), A.sum(0), atol=1e-9)
+    c = np.array([3.0, -1.0, 2.0])
+    Xt, _, _, _ = ssnal.solve(A + c, edges, w, g, tol=1e-12, q=q)
+    np.testing.assert_allclose(Xt, X + c, atol=1e-9)
+    s = 2.5
+    Xs, _, _, _ = ssnal.solve(s * A, edges, w, s * g, tol=1e-12, q=q)
+    np.testing.assert_allclose(Xs, s * X, atol=1e-8)
+    S = np.array([[0.0, -1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])  # signed permutation
+    Xq, _, _, _ = ssnal.solve(A @ S, edges, w, g, tol=1e-12, q=q)
+    np.testing.assert_allclose(Xq, X @ S, atol=1e-9)
+
+
+@pytest.mark.parametrize("q", [1, np.inf])
+def test_separable_norms_large_gamma_centroids(q):
+    """Large gamma fuses each connected component to its centroid for every norm."""
+    A, edges, _ = _small_problem(seed=42, n=20, d=2, k=4)
+    w = np.ones(edges.shape[0])      # unit weights: gamma = 100 is far past full fusion
+    X, _, _, info = ssnal.solve(A, edges, w, 100.0, tol=1e-12, q=q)
+    assert info["kkt"] <= 1e-11
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    n = A.shape[0]
+    _, comp = connected_components(coo_matrix((np.ones(len(edges)), (edges[:, 0], edges[:, 1])),
+                                              shape=(n, n)), directed=False)
+    for c in np.unique(comp):
+        sel = comp == c
+        np.testing.assert_allclose(X[sel], np.tile(A[sel].mean(0), (sel.sum(), 1)), atol=1e-8)
