@@ -308,7 +308,8 @@ def form_qnorm(args):
     for q in args.qs.split(","):
         def step():
             E, w, _ = ccm.build_graph(At, wl.k, wl.phi)
-            return ccm.solve_path(At, E, w, gam, q=q, tol=SOLVE_TOL)
+            kw = {"sigma_max": args.sigma_max} if args.sigma_max > 0 else {}
+            return ccm.solve_path(At, E, w, gam, q=q, tol=SOLVE_TOL, **kw)
         if args.warmup > 0:
             step()
         ms, (_, _, _, st) = _time(step, stream, args.steps)
@@ -323,7 +324,7 @@ def form_qnorm(args):
               flush=True)
     line = {"form": "qnorm", "metric": "gamma-solves/s for q = " + args.qs + " (graph build + path)",
             "unit": "gamma-solves/s", "workload": args.workload, "gammas": len(gam),
-            "tol": SOLVE_TOL,
+            "tol": SOLVE_TOL, "sigma_max": args.sigma_max if args.sigma_max > 0 else "default",
             **out}
     print(json.dumps(line), flush=True)
     return 0
@@ -341,6 +342,8 @@ def main():
                     help="synthetic workload (default: the MNIST-shaped one)")
     ap.add_argument("--n-gamma", type=int, default=0,
                     help="solve only the first N gammas of the path (profiling runs)")
+    ap.add_argument("--sigma-max", type=float, default=0.0,
+                    help="penalty cap passed to the solver in the qnorm form (0: library default)")
     ap.add_argument("--qs", default="2,1,inf",
                     help="comma-separated q values of the qnorm form (1, 2, inf)")
     ap.add_argument("--gamma-from", type=int, default=0,

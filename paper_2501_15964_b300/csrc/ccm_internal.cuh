@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ccm.h"
@@ -58,6 +59,10 @@ struct Ctx {
   std::vector<cudaEvent_t> ev_pool;
   ccm_profile last_profile = {};
   int64_t launches = 0;          // kernels launched by this context (all calls)
+  // dynamic shared-memory limit already raised per kernel, keyed by the kernel's
+  // host address as seen by the launching translation unit (each .cu file holds
+  // its own instance of a template kernel, so one kernel name can have several)
+  std::vector<std::pair<const void*, size_t>> smem_attr;
 };
 
 // Count one kernel launch on context c (for launch statistics).

@@ -522,13 +522,19 @@ inline int ring_plan(Ctx* c, int L, int ld, const int64_t* off, int64_t n, RingP
   return CCM_OK;
 }
 
-template <typename Tc>
-inline int set_attr_once(const void* fn, size_t smem, int device, size_t* table) {
-  size_t& cur = table[device & 63];
-  if (cur < smem) {
-    CCM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cur = smem;
+// Raise the dynamic shared-memory limit of kernel fn to smem on c's device,
+// once per (context, kernel instance).
+inline int set_smem_limit(Ctx* c, const void* fn, size_t smem) {
+  for (auto& e : c->smem_attr) {
+    if (e.first != fn) continue;
+    if (e.second < smem) {
+      CCM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      e.second = smem;
+    }
+    return CCM_OK;
   }
+  CCM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  c->smem_attr.emplace_back(fn, smem);
   return CCM_OK;
 }
 
@@ -539,9 +545,8 @@ inline int launch_matvec(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, Tc* 
                          const RingPlan& rp, double sigma, int64_t n, int ld, double* part,
                          Ctl* ctl, cudaStream_t s) {
   if (L == 32 && rp.on()) {
-    static size_t attr[64] = {};
     auto fn = k_cg_matvec_ring<CH, Tc, kRingStages>;
-    CCM_TRY(set_attr_once<Tc>((const void*)fn, rp.sh.smem_op, c->device, attr));
+    CCM_TRY(set_smem_limit(c, (const void*)fn, rp.sh.smem_op));
     fn<<<c->num_sms, rp.sh.nw * 32, rp.sh.smem_op, s>>>(R, Minv, Dg, W, Yh, meta, off, inc,
                                                         rp.spans, (Tc*)rp.parts, rp.cnt, sigma,
                                                         ld, part, ctl);
@@ -560,9 +565,8 @@ inline int launch_node_grad(Ctx* c, const double* X, const double* Ap, const dou
                             const RingPlan& rp, int64_t n, int ld, double* part, Ctl* ctl,
                             cudaStream_t s) {
   if (L == 32 && rp.on()) {
-    static size_t attr[64] = {};
     auto fn = k_node_grad_ring<CH, Tc, kRingStages>;
-    CCM_TRY(set_attr_once<Tc>((const void*)fn, rp.sh.smem_grad, c->device, attr));
+    CCM_TRY(set_smem_limit(c, (const void*)fn, rp.sh.smem_grad));
     fn<<<c->num_sms, rp.sh.nw * 32, rp.sh.smem_grad, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma,
                                                           d, G, Minv, rp.spans,
                                                           (double*)rp.parts, rp.pdiag, rp.cnt, ld,

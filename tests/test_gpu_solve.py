@@ -190,3 +190,35 @@ def test_long_rows_degenerate_graphs(ccm, precision):
     assert np.linalg.norm(X2[0] - want0) <= 1e-6 * np.linalg.norm(want0)
     assert np.linalg.norm(X2[1] - want1) <= 1e-6 * np.linalg.norm(want1)
     assert lab2.cpu().tolist() == [[0, 1], [0, 0]]
+
+
+_SHARED_KERNEL_SCRIPT = r"""
+import numpy as np, torch
+import paper_2501_15964_b300 as ccm
+rng = np.random.default_rng(5)
+cent = rng.normal(0, 2, size=(3, 150))
+A = cent[rng.integers(0, 3, 40)] + rng.normal(size=(40, 150))
+At = torch.tensor(A, device="cuda:0")
+E, w, _ = ccm.build_graph(At, 4)
+# the FP64 long-row ring kernels need more than 48 KB of dynamic shared memory;
+# ADMM and SSNAL launch them from different translation units
+_, _, _, st = ccm.solve_path_admm(At, E, w, [1.0], tol=1e-6, precision=0)
+assert all(s["status"] == 0 for s in st), st
+for q in (2, 1, "inf"):
+    _, _, _, st = ccm.solve_path(At, E, w, [0.5, 2.0], q=q, tol=1e-6, precision=0)
+    assert all(s["status"] == 0 for s in st), (q, st)
+print("ok")
+"""
+
+
+def test_ring_kernels_after_another_solver_in_a_fresh_process(ccm):
+    """The ring kernels' shared-memory limit is raised per kernel instance: an
+    ADMM solve followed by SSNAL solves (q = 2, 1, inf) on FP64 long rows in a new
+    process, where no earlier launch has set anything."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _SHARED_KERNEL_SCRIPT], cwd=root,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
