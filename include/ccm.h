@@ -54,7 +54,8 @@ typedef enum { CCM_ENGINE_AUTO = 0, CCM_ENGINE_GRID = 1, CCM_ENGINE_BLOCK = 2 } 
 /* Solver options; fill with ccm_default_options() and override fields. */
 typedef struct {
   double sigma0;          /* initial augmented-Lagrangian penalty (default 1) */
-  double sigma_max;       /* cap on the penalty (default 10) */
+  double sigma_max;       /* cap on the penalty; <= 0 (the default) selects 10 for
+                             q = 2 and 1 for q = 1 and q = inf (at least sigma0) */
   int32_t max_outer;      /* multiplier updates per gamma (default 200) */
   int32_t max_newton;     /* semismooth-Newton steps per multiplier update (default 50) */
   int32_t max_cg;         /* CG iterations per Newton step (default 500) */

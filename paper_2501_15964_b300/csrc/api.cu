@@ -151,7 +151,7 @@ int32_t ccm_max_dim(void) { return 1024; }
 void ccm_default_options(ccm_options* o) {
   if (!o) return;
   o->sigma0 = 1.0;
-  o->sigma_max = 10.0;
+  o->sigma_max = 0.0;  // automatic: resolve_sigma_max()
   o->max_outer = 200;
   o->max_newton = 50;
   o->max_cg = 500;

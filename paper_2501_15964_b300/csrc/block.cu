@@ -829,6 +829,7 @@ extern "C" int ccm_solve_path_batched(ccm_ctx* x, int32_t P, const ccm_problem* 
   ccm_options o;
   ccm_default_options(&o);
   if (opt) o = *opt;
+  o.sigma_max = resolve_sigma_max(o, 2);
   CCM_CUDA(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<HostProblem> hp(P);

@@ -76,6 +76,16 @@ int host_scalars(Ctx* c, size_t bytes, void** out);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Penalty cap: a positive option value as given; otherwise 10 for q = 2 and 1
+// for q = 1 and q = inf (the separable-ball norms converged in far fewer Newton
+// and CG steps with the lower cap on the measured paths), and never below the
+// initial penalty sigma0.
+inline double resolve_sigma_max(const ccm_options& o, int q) {
+  if (o.sigma_max > 0) return o.sigma_max;
+  const double cap = q == 2 ? 10.0 : 1.0;
+  return o.sigma0 > cap ? o.sigma0 : cap;
+}
+
 // ---------------------------------------------------------------- device helpers
 template <typename T> struct Vec4;
 template <> struct Vec4<double> {

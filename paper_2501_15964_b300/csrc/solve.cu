@@ -569,6 +569,7 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
   ccm_options o;
   ccm_default_options(&o);
   if (opt) o = *opt;
+  o.sigma_max = resolve_sigma_max(o, q);
   if (o.max_outer < 1 || o.max_newton < 1 || o.max_cg < 1 || !(o.sigma0 > 0) ||
       !(o.sigma_max >= o.sigma0)) {
     set_error("ccm_solve_path: invalid options");
