@@ -64,3 +64,19 @@ def test_package_has_no_cpu_fallback():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_constants_match_header():
+    """The Python binding's q = inf code and the option defaults agree with the
+    C header (sigma_max <= 0 selects the per-q penalty cap)."""
+    import ctypes as C
+    from paper_2501_15964_b300._lib import Q_INF, Options
+    from paper_2501_15964_b300.api import _q_arg
+    src = open(HEADER).read()
+    m = re.search(r"#define\s+CCM_Q_INF\s+(\d+)", src)
+    assert m and int(m.group(1)) == Q_INF == 2 ** 31 - 1
+    assert _q_arg("inf") == _q_arg(float("inf")) == Q_INF and _q_arg(1) == 1
+    import paper_2501_15964_b300 as ccm
+    o = Options()
+    ccm.load_library().ccm_default_options(C.byref(o))
+    assert o.sigma_max <= 0.0 and o.sigma0 == 1.0
