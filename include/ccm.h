@@ -1,12 +1,13 @@
 /*
- * ccm.h - C ABI of libccm: convex clustering (model CCM, q = 2) along a
+ * ccm.h - C ABI of libccm: convex clustering (model CCM; q = 2, 1 or inf) along a
  * gamma path on one NVIDIA B300 (sm_103a).
  *
  * Model (Sec. 1, model CCM): given points a_1..a_n in R^d, weights
  * w_ij = w_ji >= 0 and gamma >= 0,
- *     X*(gamma) = argmin_X 1/2 sum_i ||x_i - a_i||^2 + gamma sum_{i<j} w_ij ||x_i - x_j||_2 ,
- * solved for a non-decreasing sequence gamma_1 <= ... <= gamma_T (the
- * clustering path); a_i and a_j share a cluster when x_i* = x_j*.
+ *     X*(gamma) = argmin_X 1/2 sum_i ||x_i - a_i||^2 + gamma sum_{i<j} w_ij ||x_i - x_j||_q ,
+ * q = 2 (default), 1 or inf (ccm_solve_path only), solved for a non-decreasing
+ * sequence gamma_1 <= ... <= gamma_T (the clustering path); a_i and a_j share a
+ * cluster when x_i* = x_j*.
  *
  * Conventions for every function below:
  *   - Arrays are DEVICE pointers unless marked "host", row-major, owned and

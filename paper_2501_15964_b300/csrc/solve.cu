@@ -1,4 +1,4 @@
-// ccm_solve_path: SSNAL for model CCM (q = 2) along a gamma path, grid engine.
+// ccm_solve_path: SSNAL for model CCM (q = 2, 1 or inf) along a gamma path, grid engine.
 //
 // The outer loop (multiplier updates), the semismooth-Newton loop, the
 // Armijo line search and the CG loop are driven from the host; every

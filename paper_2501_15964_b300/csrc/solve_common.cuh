@@ -21,7 +21,7 @@ struct SolveArgs {
   ccm_stats* stats = nullptr;      // host
   const double* X0 = nullptr;
   const double* U0 = nullptr;
-  int q = 2;  // norm of the differences: 2 (group lasso) or 1 (elementwise)
+  int q = 2;  // norm of the differences: 2 (group lasso), 1 (elementwise) or CCM_Q_INF (max)
 
   // Algorithmic bytes of one Newton-CG operator launch (each datum once):
   // R read and W written (n x ld each), Minv (n), the yhat rows of the m_out

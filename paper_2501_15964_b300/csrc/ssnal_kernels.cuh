@@ -1,4 +1,5 @@
-// SSNAL building blocks for model CCM, q = 2 (Sec. 1 names the method).
+// SSNAL building blocks for model CCM, q = 2 (Sec. 1 names the method); the q = 1
+// and q = inf edge passes and their Jacobian kinds are at the end of this file.
 //
 // Notation (restated from convex analysis; the paper prints no formulas for
 // SSNAL): edges l = (i, j), i < j; (BX)_l = x_i - x_j; r_l = gamma w_l;
