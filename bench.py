@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "mnist10k_d784"
+NOMINAL_HBM_GBS = 7700.0   # B300 HBM3e nominal bandwidth, for the second roofline denominator
 TOL = 1e-6          # metric threshold on KKT and relative gap
 SOLVE_TOL = 2e-7    # solver stop: tighter, so X is within 1e-6 of the oracle
 METRIC = "gamma-solves/s at KKT<=1e-6 (graph build + path solve)"
@@ -462,6 +463,8 @@ def main():
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
+                         "nominal_peak": NOMINAL_HBM_GBS,
                          "launches_timed": int(mv_n),
                          "ms_per_step": mv_ms / args.steps, "traffic": None},
             "e2e": {"value": e2e, "unit": "gamma-solves/s",
