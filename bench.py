@@ -3,8 +3,9 @@
 One step = the whole hot path on one synthetic problem: build the exact
 symmetrized kNN graph with Gaussian weights (ccm_build_graph) and solve the
 warm-started gamma path to KKT <= 1e-6 and relative gap <= 1e-6 with labels
-(ccm_solve_path). Default workload: the MNIST-shaped stand-in (n = 10,000,
-d = 784, k = 10, phi = 1/median, 50 gammas in [1e-3, 1e2]).
+(ccm_solve_path). Default workload: the largest single-GPU one, a
+100-component Gaussian mixture with n = 200,000 points in d = 50, k = 10,
+phi = 0.5, 30 gammas in [1e-3, 1e2] (`--workload` selects another).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {ccm,reference}]
 
@@ -32,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "mnist10k_d784"
+WORKLOAD = "gmm200k_d50"
 NOMINAL_HBM_GBS = 7700.0   # B300 HBM3e nominal bandwidth, for the second roofline denominator
 TOL = 1e-6          # metric threshold on KKT and relative gap
 SOLVE_TOL = 2e-7    # solver stop: tighter, so X is within 1e-6 of the oracle
@@ -96,17 +97,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_problem(seed, workload=WORKLOAD):
-    A, _, wl = synth.make_workload(workload, seed)
+def make_problem(seed, workload=None):
+    A, _, wl = synth.make_workload(workload or WORKLOAD, seed)
     gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
     return A, wl, gam
 
 
-def run_oracle_sample(seed, n_gamma=24):
-    """CPU oracle on a bounded, fixed sample: the same recipe at n = 300 points,
-    the first `n_gamma` gammas of the grid (the same work every call; about 14 s
-    on one core, the next gamma alone would take about 45 s). Returns
-    (gamma-solves/s, description, BLAS threads)."""
+# Bounded samples of each recipe for the CPU oracle (points, gammas from the
+# start of the grid; None = all), sized for about 5-15 s on one core so that the
+# reference arm's 25 default driver steps end within a few minutes: the
+# n = 200,000 recipe at phi = 0.5 barely fuses and the oracle solves 3,000 of its
+# points over all 30 gammas in about 6 s; with phi = 1/median it fuses and 500
+# points take about 11 s; on the MNIST-shaped recipe the 25th gamma alone takes
+# about 45 s at 300 points, so that sample stops after 24.
+ORACLE_SAMPLE = {"gmm200k_d50": (3000, None), "gmm200k_d50_medphi": (500, None),
+                 "mnist10k_d784": (300, 24)}
+
+
+def run_oracle_sample(seed):
+    """CPU oracle on a bounded, fixed sample of the bench workload's recipe (the
+    same work every call). Returns (gamma-solves/s, description, BLAS threads)."""
     import contextlib
     try:
         from threadpoolctl import threadpool_limits
@@ -118,23 +128,24 @@ def run_oracle_sample(seed, n_gamma=24):
 
     from oracle import graph as og
     from oracle import ssnal as osn
-    n_s = 300
-    A, _, wl = synth.make_workload(WORKLOAD, seed, n=n_s)
+    n_s, n_gamma = ORACLE_SAMPLE.get(WORKLOAD, (500, None))
+    A, _, wl = synth.make_workload(WORKLOAD, seed, n=min(n_s, synth.WORKLOADS[WORKLOAD].n))
     gam = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    gam_s = gam[:n_gamma] if n_gamma else gam
     with limit:
         t0 = time.perf_counter()
         edges, w, _ = og.build_graph(A, wl.k, wl.phi)
         X = U = None
         sigma = 1.0
-        for g in gam[:n_gamma]:
+        for g in gam_s:
             # same penalty cap as the library's default for q = 2; iteration caps
             # keep one gamma bounded
             X, U, sigma, _ = osn.solve(A, edges, w, g, X, U, sigma, tol=TOL, sigma_max=10.0,
                                        max_outer=100, max_newton=30)
         el = time.perf_counter() - t0
-    done = min(n_gamma, len(gam))
-    return done / el, (f"oracle graph + SSNAL path on n={n_s} points of the {WORKLOAD} recipe "
-                       f"(d={A.shape[1]}, k={wl.k}), first {done} of {len(gam)} gammas, "
+    done = len(gam_s)
+    return done / el, (f"oracle graph + SSNAL path on n={A.shape[0]} points of the {WORKLOAD} "
+                       f"recipe (d={A.shape[1]}, k={wl.k}), first {done} of {len(gam)} gammas, "
                        f"tol 1e-6, {el:.1f} s, BLAS threads {threads}"), threads
 
 
@@ -455,7 +466,7 @@ def main():
             "dtype": "f64 (CG operator f32)" if prec == 1 else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": int(A.shape[0]), "d": int(A.shape[1]),
-                       "k": wl.k, "phi": "1/median", "gammas": T, "tol": SOLVE_TOL,
+                       "k": wl.k, "phi": (wl.phi if wl.phi > 0 else "1/median"), "gammas": T, "tol": SOLVE_TOL,
                        "edges": int(E.shape[0]),
                        "l2": "inputs larger than L2 (per-step working set > 1 GB)",
                        "parallelism": f"replicas x{world}"},

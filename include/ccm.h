@@ -65,7 +65,9 @@ typedef struct {
                              CG dot product; gradient, line search, multiplier update,
                              KKT and gap in float64. FP64: everything float64. */
   int32_t engine;         /* ccm_engine. GRID: one problem across the whole GPU;
-                             BLOCK: one thread block runs the whole path (small n). */
+                             BLOCK: one thread block runs the whole path (small n; q = 2,
+                             d <= 128, no warm start: X0 / U0 make AUTO pick GRID and
+                             BLOCK return CCM_ERR_UNSUPPORTED). */
   int32_t profile;        /* 1: time every Newton-CG operator launch with CUDA events
                              (read back with ccm_last_profile) */
   const double* X0;       /* optional device n x d warm start for the first gamma, or NULL */
@@ -222,11 +224,14 @@ int ccm_labels(ccm_ctx* ctx, const double* X, int64_t n, int32_t d, const int32_
  * The caller still passes X (n x d), the edges (m x 2) and labels (n int32), all
  * device pointers; *n_clusters (host, may be NULL) receives the cluster count.
  * n above 262,144 returns CCM_ERR_INVALID_ARG with a message naming the limit.
- * The first call on a device (with that device current) looks up the scratch
- * address with cudaGetSymbolAddress: make that first call before any stream
- * capture. All calls share the one scratch array, so calls that can overlap on
- * the GPU (different streams or host threads) race: serialise them. The call
- * synchronises `stream` before returning.
+ * Every call looks up the scratch address of the current device with
+ * cudaGetSymbolAddress (so the address stays valid across cudaDeviceReset);
+ * the first call on a device also loads the module, so make that first call
+ * before any stream capture. All calls share the one scratch array, so calls
+ * that can overlap on the GPU (different streams or host threads) race:
+ * serialise them. The call synchronises `stream` before returning, so `stream`
+ * must not be under capture, and must not be the legacy NULL stream while
+ * another stream of the device captures in global mode.
  */
 int ccm_labels_noalloc(const double* X, int64_t n, int32_t d, const int32_t* edges, int64_t m,
                        int32_t* labels, int32_t* n_clusters, ccm_stream_t stream);

@@ -51,11 +51,25 @@ __global__ void k_check_finite(const double* __restrict__ A, int64_t total, int*
 }
 
 // column means (one thread per column, rows in order: deterministic)
-__global__ void k_colmean(const double* __restrict__ A, int64_t n, int d, double* __restrict__ mu) {
+// Column means in two fixed-order passes: block b sums the rows
+// [b R, (b+1) R) of every column (consecutive threads read consecutive columns
+// of a row), then one thread per column adds the block partials in block order.
+__global__ void k_colsum_part(const double* __restrict__ A, int64_t n, int d, int64_t R,
+                              double* __restrict__ part) {
+  const int64_t i0 = (int64_t)blockIdx.x * R, i1 = min(n, i0 + R);
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    double s = 0.0;
+    for (int64_t i = i0; i < i1; ++i) s += A[i * d + k];
+    part[(int64_t)blockIdx.x * d + k] = s;
+  }
+}
+
+__global__ void k_colmean(const double* __restrict__ part, int nparts, int64_t n, int d,
+                          double* __restrict__ mu) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d) return;
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += A[i * d + k];
+  for (int b = 0; b < nparts; ++b) s += part[(int64_t)b * d + k];
   mu[k] = s / (double)n;
 }
 
@@ -416,11 +430,16 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   // 1. centre
   CCM_TRY(ws_get(c, S_AP, (size_t)n_pad * ldf * 4 + 16, &p));
   float* At = (float*)p;
-  CCM_TRY(ws_get(c, S_X0, (size_t)d * 8 + (size_t)n * 8 + 64, &p));
+  const int64_t rows_per_part = 256;
+  const int nparts = (int)((n + rows_per_part - 1) / rows_per_part);
+  CCM_TRY(ws_get(c, S_X0, ((size_t)round_up(d, 8) + (size_t)n + 8 + (size_t)nparts * d) * 8, &p));
   double* mu = (double*)p;
   double* nrm = mu + round_up(d, 8);
   double* nmax = nrm + n;
-  k_colmean<<<(d + 127) / 128, 128, 0, s>>>(A, n, d, mu);
+  double* colpart = nmax + 8;
+  k_colsum_part<<<nparts, 128, 0, s>>>(A, n, d, rows_per_part, colpart);
+  CCM_COUNT(c);
+  k_colmean<<<(d + 127) / 128, 128, 0, s>>>(colpart, nparts, n, d, mu);
   CCM_COUNT(c);
   k_center<<<nb(n_pad), threads, 0, s>>>(A, n, d, ldf, mu, At, nrm, n_pad);
   CCM_COUNT(c);

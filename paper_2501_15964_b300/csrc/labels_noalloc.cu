@@ -15,7 +15,6 @@
 // any stream capture. Every call reuses the same array, so calls that can
 // overlap on the GPU (different streams, or different host threads) race and
 // must be serialised by the caller.
-#include <mutex>
 
 #include "ccm_internal.cuh"
 
@@ -104,23 +103,20 @@ k_na_rank(int64_t n, NoAllocScratch* sc, int32_t* __restrict__ labels) {
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) labels[i] = sc->rank[sc->parent[i]];
 }
 
-// device address of the static scratch, looked up once per device
-static std::mutex g_noalloc_mu;
-static NoAllocScratch* g_noalloc_ptr[128] = {};
-
+// Device address of the static scratch on the current device. Looked up on
+// every call (a host-side table lookup once the module is loaded; it allocates
+// nothing), so a context destroyed and re-created by cudaDeviceReset never
+// leaves a stale address behind. The first lookup on a device loads the module
+// and is the reason the first call must come before any stream capture.
 static int noalloc_scratch(int device, NoAllocScratch** out) {
-  if (device < 0 || device >= 128) {
+  if (device < 0) {
     set_error("ccm_labels_noalloc: device %d out of range", device);
     return CCM_ERR_INVALID_ARG;
   }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
-    g_noalloc_ptr[device] = (NoAllocScratch*)ptr;
-  }
-  *out = g_noalloc_ptr[device];
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+  *out = (NoAllocScratch*)ptr;
   return CCM_OK;
 }
 

@@ -243,6 +243,11 @@ struct GridEngine {
       return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, maxb));
     };
     const int b_edge = (int)std::max<int64_t>(1, std::min<int64_t>((m + gpb - 1) / gpb, maxb));
+    // the q = 2 edge passes run in their own (narrower) group shape
+    using ES = EdgeShape<L, CH>;
+    const int gpb_e = threads / ES::L;
+    const int b_edge2 =
+        (int)std::max<int64_t>(1, std::min<int64_t>((m + gpb_e - 1) / gpb_e, 2 * maxb));
     const int b_elem = nb(nl);
     const int b_quad = nb((nl + 3) / 4);
 
@@ -338,8 +343,8 @@ struct GridEngine {
         k_edge_eval_qn<kQInf, L, CH, Tc><<<b_edge, threads, 0, s>>>(
             Xc, U, edges, a.w, gamma_cur, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
       else
-        k_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(Xc, U, edges, a.w, gamma_cur, sigma,
-                                                          Ut, Yh, alpha, kind, m, ld, part, ctl);
+        k_edge_eval<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
+            Xc, U, edges, a.w, gamma_cur, sigma, Ut, Yh, alpha, kind, m, ld, part, ctl);
       CCM_COUNT(c);
       CCM_TRY(launch_node_grad<L, CH, Tc>(c, Xc, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv,
                                           rp, n, ld, part, ctl, s));
@@ -445,9 +450,8 @@ struct GridEngine {
           k_kkt_edge_eval_qn<kQInf, L, CH, Tc><<<b_edge, threads, 0, s>>>(
               X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
         else
-          k_kkt_edge_eval<L, CH, Tc><<<b_edge, threads, 0, s>>>(X, U, edges, a.w, gamma, sigma,
-                                                                Ut, Yh, alpha, kind, m, ld, part,
-                                                                ctl);
+          k_kkt_edge_eval<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
+              X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, ld, part, ctl);
         CCM_COUNT(c);
         edge_ready = true;
         edge_sigma = sigma;
@@ -588,10 +592,12 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
   // otherwise the grid engine spreads every phase over the whole GPU
   const int64_t ldd = round_up(d, 4);
   const bool small = n * ldd <= 16384 && m * ldd <= 131072 && d <= 128;
+  // the block engine starts every path cold: a warm start (X0 / U0) runs on the grid engine
+  const bool warm = o.X0 != nullptr || o.U0 != nullptr;
   const bool use_block =
-      o.engine == CCM_ENGINE_BLOCK || (o.engine == CCM_ENGINE_AUTO && small && q == 2);
-  if (o.engine == CCM_ENGINE_BLOCK && (d > 128 || q != 2)) {
-    set_error("ccm_solve_path: the block engine supports q = 2 and d <= 128");
+      o.engine == CCM_ENGINE_BLOCK || (o.engine == CCM_ENGINE_AUTO && small && q == 2 && !warm);
+  if (o.engine == CCM_ENGINE_BLOCK && (d > 128 || q != 2 || warm)) {
+    set_error("ccm_solve_path: the block engine supports q = 2, d <= 128 and no warm start");
     return CCM_ERR_UNSUPPORTED;
   }
   if (use_block) {

@@ -60,6 +60,43 @@ __device__ __forceinline__ float f64_to_f32_rz(double x) {
   const unsigned mag = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
   return __uint_as_float((hi & 0x80000000u) | (e > 896u ? mag : 0u));
 }
+// float32 -> float64, exact, from the bit fields (normal, finite x only): the
+// sign and the 23 fraction bits move over unchanged, the exponent is re-biased
+// from 127 to 1023. Integer operations only (see f64_to_f32_rz).
+__device__ __forceinline__ double f32_to_f64_normal(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = ((b >> 23) & 0xffu) + 896u;
+  const unsigned hi = (b & 0x80000000u) | (e << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// 1/sqrt(s) for s > 0 to about 1e-13 relative: a float32 hardware estimate
+// (error about 2^-22 after the truncation of s to float32) refined by one
+// Newton step for f(x) = 1/x^2 - s in float64,
+//   x1 = x0 + (x0/2)(1 - s x0^2),
+// whose relative error is about (3/2) e0^2. That costs four float64 operations
+// against the twenty or so of a correctly rounded square root and division,
+// which matters on B300 whose FP64 pipe (2 operations per clock per SM) bounds
+// the edge passes. Outside [1e-36, 1e36], where the float32 estimate could
+// overflow or lose precision, it takes 1/sqrt(s) in float64.
+__device__ __forceinline__ double rsqrt_refined(double s) {
+  if (!(s > 1e-36 && s < 1e36)) return 1.0 / sqrt(s);
+  const double x0 = f32_to_f64_normal(rsqrtf(f64_to_f32_rz(s)));
+  const double e = fma(-(s * x0), x0, 1.0);
+  return fma(0.5 * x0, e, x0);
+}
+
+// Group shape of the q = 2 edge passes for an operator shape (LANES, CH). Those
+// passes do per-edge scalar work (three norms, their inverse square roots, the
+// ball test, h) in every lane of the edge's group, so for short rows (one quad
+// per lane) each lane takes four quads and the group is four times narrower:
+// fewer lanes repeat the scalar work and the group sums have fewer levels.
+template <int LANES, int CH>
+struct EdgeShape {
+  static constexpr int L = (CH == 1 && LANES >= 4) ? LANES / 4 : (CH == 1 && LANES == 2 ? 1 : LANES);
+  static constexpr int C = CH * LANES / L;
+};
+
 template <typename Tc>
 __device__ __forceinline__ Tc to_operator(double x);
 template <>
@@ -97,7 +134,9 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
         ss = fma(y[c][k], y[c][k], ss);
       }
     ss = group_sum<LANES>(ss, mask);
-    double ny = sqrt(ss);
+    // ||y|| and 1/||y|| from one refined inverse square root (ss = 0: y = 0, inside)
+    const double rs = ss > 0.0 ? rsqrt_refined(ss) : 0.0;
+    const double ny = ss * rs;
     uint8_t kd;
     double scale, a;
     if (!(r > 0.0)) {
@@ -105,7 +144,7 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
     } else if (ny <= r) {
       kd = K_IN; scale = 1.0; a = 1.0;
     } else {
-      kd = K_OUT; scale = r / ny; a = r / ny;
+      kd = K_OUT; scale = r * rs; a = scale;
     }
     double h = (ny <= r) ? 0.5 * ss : r * ny - 0.5 * r * r;
     if (lane == 0) {
@@ -126,8 +165,7 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
     if (kd == K_OUT) {
       // yhat in the operator's precision: for float32 the scaling runs in
       // float32 (FP64 throughput is the limit of this kernel)
-      const double inv = 1.0 / ny;
-      const Tc invc = (Tc)inv;
+      const Tc invc = to_operator<Tc>(rs);
       Tc yh[CH][4];
 #pragma unroll
       for (int c = 0; c < CH; ++c)
@@ -145,7 +183,26 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
 
 // ------------------------------------------------------------ node gradient
 // G_i = x_i - a_i + sum_l +-Ut_l ; also Jacobi scalars Minv_i = 1/(1 + sigma sum_l t_l)
-// with t_l = 1 (inside) or alpha_l (d-1)/d (outside) = trace(P_l)/d.
+// with t_l = trace(P_l)/d: 1 (inside), alpha_l (d-1)/d (outside), alpha_l (q = 1
+// mask, q = inf l1-ball kinds), 0 (inert).
+//
+// Register form (rows of at most 32 quads per group). Memory-level parallelism:
+// a group reads its node's incidence records LANES at a time, one per lane
+// (coalesced), and then gathers kNB incident rows at once before adding them,
+// so a lane keeps kNB row loads in flight instead of one. The rows are still
+// added one by one in increasing edge id (the same order for every run).
+template <int CH>
+struct GatherDepth {
+  static constexpr int v = CH == 1 ? 4 : (CH == 2 ? 2 : 1);
+};
+
+template <typename Tc>
+__device__ __forceinline__ double trace_term(uint8_t kd, Tc al, double tr_out) {
+  return kd == K_IN ? 1.0
+         : (kd == K_OUT ? (double)al * tr_out
+                        : ((kd == K_MASK || kd == K_LINF) ? (double)al : 0.0));
+}
+
 template <int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
 k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
@@ -153,63 +210,67 @@ k_node_grad(const double* __restrict__ X, const double* __restrict__ Ap,
             const int2* __restrict__ inc, const Tc* __restrict__ alpha,
             const uint8_t* __restrict__ kind, double sigma, int d, double* __restrict__ G,
             Tc* __restrict__ Minv, int64_t n, int ld, double* partials, Ctl* ctl) {
+  constexpr int NB = GatherDepth<CH>::v;
   const int lane = threadIdx.x % LANES;
+  const unsigned mask = group_mask<LANES>();
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
   const double tr_out = (double)(d - 1) / (double)d;
   double acc[2] = {0.0, 0.0};
   for (int64_t i = g0; i < n; i += ng) {
     const int64_t b = off[i], eend = off[i + 1];
-    // one quad per lane at a time: few registers, many warps in flight; the
-    // incidence list is re-read per chunk from L1. Every element still sums
-    // its incident edges in increasing edge id (same order as before).
-#pragma unroll 1
-    for (int c = 0; c < CH; ++c) {
-      const int q = c * LANES + lane;
-      if (4 * q >= ld) break;
-      double g[4], a[4];
-      Vec4<double>::load(X + i * ld + 4 * q, g);
-      Vec4<double>::load(Ap + i * ld + 4 * q, a);
+    double g[CH][4], a4[CH][4];
+    row_load<LANES, CH>(X + i * ld, ld, lane, g);
+    row_load<LANES, CH>(Ap + i * ld, ld, lane, a4);
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        g[k] -= a[k];
-        acc[1] += 0.5 * g[k] * g[k];
+        g[c][k] -= a4[c][k];
+        acc[1] += 0.5 * g[c][k] * g[c][k];
       }
-      int64_t t = b;
-      for (; t + 1 < eend; t += 2) {  // two incidences in flight
-        const int2 e0 = inc[t], e1 = inc[t + 1];
-        double u0[4], u1[4];
-        Vec4<double>::load(Ut + (int64_t)e0.x * ld + 4 * q, u0);
-        Vec4<double>::load(Ut + (int64_t)e1.x * ld + 4 * q, u1);
-        const double s0 = (i < e0.y) ? 1.0 : -1.0, s1 = (i < e1.y) ? 1.0 : -1.0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] += s0 * u0[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] += s1 * u1[k];
+    double diag = 0.0;
+    for (int64_t base = b; base < eend; base += LANES) {
+      const int nb = (int)(eend - base < (int64_t)LANES ? eend - base : (int64_t)LANES);
+      int2 rec = make_int2(0, 0);
+      double tl = 0.0;
+      if (lane < nb) {
+        rec = inc[base + lane];
+        tl = trace_term<Tc>(kind[rec.x], alpha[rec.x], tr_out);
       }
-      if (t < eend) {
-        const int2 e0 = inc[t];
-        double u0[4];
-        Vec4<double>::load(Ut + (int64_t)e0.x * ld + 4 * q, u0);
-        const double s0 = (i < e0.y) ? 1.0 : -1.0;
+      diag += group_sum<LANES>(tl, mask);
+      for (int j = 0; j < nb; j += NB) {
+        double u[NB][CH][4];
+        double sg[NB];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] += s0 * u0[k];
+        for (int kk = 0; kk < NB; ++kk) {
+          const int ex = __shfl_sync(mask, rec.x, j + kk, LANES);
+          const int ey = __shfl_sync(mask, rec.y, j + kk, LANES);
+          sg[kk] = (i < ey) ? 1.0 : -1.0;
+          if (j + kk < nb) {
+            row_load<LANES, CH>(Ut + (int64_t)ex * ld, ld, lane, u[kk]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+              for (int k = 0; k < 4; ++k) u[kk][c][k] = 0.0;
+            sg[kk] = 0.0;
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < NB; ++kk)
+#pragma unroll
+          for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[c][k] += sg[kk] * u[kk][c][k];
       }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[0] += g[k] * g[k];
-      Vec4<double>::store(G + i * ld + 4 * q, g);
     }
-    if (lane == 0) {
-      double diag = 0.0;
-      for (int64_t t = b; t < eend; ++t) {
-        const int e = inc[t].x;
-        const uint8_t kd = kind[e];
-        diag += kd == K_IN ? 1.0
-                : (kd == K_OUT ? (double)alpha[e] * tr_out
-                               : ((kd == K_MASK || kd == K_LINF) ? (double)alpha[e] : 0.0));
-      }
-      Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
-    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[0] += g[c][k] * g[c][k];
+    row_store<LANES, CH>(G + i * ld, ld, lane, g);
+    if (lane == 0) Minv[i] = (Tc)(1.0 / (1.0 + sigma * diag));
   }
   double tot[2];
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_N], tot) && threadIdx.x == 0) {
@@ -300,9 +361,75 @@ __device__ __forceinline__ void cg_set_alpha(Ctl* ctl, double delta) {
 // W = D u + sigma B^T P B u with u = Minv R (D = I, or the diagonal Dg);
 // delta = <W, u>. Node-parallel pull over the CSR of B^T: a group of LANES
 // threads owns node i and visits its incidences in increasing edge id,
-// gathering the other endpoint's R row (and yhat_l for outside edges) into
-// registers. Used for short rows and the adjoint; k_cg_matvec_ring stages long
-// rows through shared memory.
+// gathering the other endpoint's R row (and the yhat / mask / s row of the edge
+// for the kinds that have one). Like k_node_grad, the group reads its node's
+// incidence records and packed coefficients LANES at a time (one per lane) and
+// keeps kNB gathered rows in flight; the terms are still added in edge-id
+// order. Used for short rows and the adjoint; k_cg_matvec_ring stages long rows
+// through shared memory. The dot product <W, u> is accumulated exactly in
+// float-float form (two_prod / two_sum) per lane, then in float64.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  // s + e += x with the rounding error of s + x kept in e (Knuth's two-sum)
+  const float t = s + x;
+  const float bp = t - s;
+  e += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+__device__ __forceinline__ void dot_acc(float& s, float& e, float a, float b) {
+  const float p = a * b;
+  e += fmaf(a, b, -p);  // exact product error (fused multiply-add)
+  two_sum_acc(s, e, p);
+}
+__device__ __forceinline__ void dot_acc(double& s, double& e, double a, double b) {
+  s = fma(a, b, s);
+}
+
+template <int LANES, int CH, typename Tc>
+__device__ __forceinline__ void matvec_term(Tc c, Tc mo, const Tc (&u)[CH][4], const Tc (&v0)[CH][4],
+                                            const Tc (&yh)[CH][4], Tc (&accv)[CH][4],
+                                            unsigned mask) {
+  Tc v[CH][4];
+#pragma unroll
+  for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[cc][k] = u[cc][k] - mo * v0[cc][k];
+  if (c > (Tc)2.5) {  // q = inf: diag(s != 0) - s s^T
+    Tc sdot = (Tc)0;
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sdot += yh[cc][k] * v[cc][k];
+    sdot = group_sum<LANES>(sdot, mask);
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        accv[cc][k] += (yh[cc][k] != (Tc)0 ? v[cc][k] : (Tc)0) - sdot * yh[cc][k];
+  } else if (c > (Tc)1.5) {  // q = 1: diagonal mask
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) accv[cc][k] += yh[cc][k] * v[cc][k];
+  } else if (c < (Tc)0) {  // outside: -c (I - yhat yhat^T)
+    Tc sdot = (Tc)0;
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sdot += yh[cc][k] * v[cc][k];
+    sdot = group_sum<LANES>(sdot, mask);
+    const Tc a = -c;
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) accv[cc][k] += a * (v[cc][k] - sdot * yh[cc][k]);
+  } else if (c > (Tc)0) {  // inside: I
+#pragma unroll
+    for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) accv[cc][k] += v[cc][k];
+  }
+}
+
 template <int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
 k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __restrict__ Dg,
@@ -310,12 +437,13 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
             const int64_t* __restrict__ off, const int2* __restrict__ inc, double sigma,
             int64_t n, int ld, double* partials, Ctl* ctl) {
   if (!ctl->cg.active) return;
+  constexpr int NB = GatherDepth<CH>::v;
   const int lane = threadIdx.x % LANES;
   const unsigned mask = group_mask<LANES>();
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
   const Tc sg = (Tc)sigma;
-  double acc[1] = {0.0};
+  Tc dot = (Tc)0, dot_e = (Tc)0;  // <W, u> over this thread's elements, float-float
   for (int64_t i = g0; i < n; i += ng) {
     Tc u[CH][4], accv[CH][4];
     const Tc mi = Minv[i];
@@ -328,83 +456,59 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
         accv[c][k] = (Tc)0;
       }
     const int64_t b = off[i], eend = off[i + 1];
-    // the next incidence and its coefficients are fetched one iteration ahead
-    int2 eo_n = make_int2(0, 0);
-    IncMeta<Tc> mm_n;
-    mm_n.c = (Tc)0;
-    mm_n.mo = (Tc)0;
-    if (b < eend) {
-      eo_n = inc[b];
-      mm_n = meta[b];
-    }
-    for (int64_t t = b; t < eend; ++t) {
-      const int2 eo = eo_n;
-      const IncMeta<Tc> mm = mm_n;
-      if (t + 1 < eend) {
-        eo_n = inc[t + 1];
-        mm_n = meta[t + 1];
+    for (int64_t base = b; base < eend; base += LANES) {
+      const int nb = (int)(eend - base < (int64_t)LANES ? eend - base : (int64_t)LANES);
+      int2 rec = make_int2(0, 0);
+      IncMeta<Tc> mm;
+      mm.c = (Tc)0;
+      mm.mo = (Tc)0;
+      if (lane < nb) {
+        rec = inc[base + lane];
+        mm = meta[base + lane];
       }
-      if (mm.c == (Tc)0) continue;
-      Tc v[CH][4];
-      row_load<LANES, CH>(R + (int64_t)eo.y * ld, ld, lane, v);
+      for (int j = 0; j < nb; j += NB) {
+        Tc v0[NB][CH][4], yh[NB][CH][4];
+        Tc cs[NB], mos[NB];
 #pragma unroll
-      for (int c = 0; c < CH; ++c)
+        for (int kk = 0; kk < NB; ++kk) {
+          const int ex = __shfl_sync(mask, rec.x, j + kk, LANES);
+          const int ey = __shfl_sync(mask, rec.y, j + kk, LANES);
+          cs[kk] = __shfl_sync(mask, mm.c, j + kk, LANES);
+          mos[kk] = __shfl_sync(mask, mm.mo, j + kk, LANES);
+          if (j + kk >= nb) cs[kk] = (Tc)0;
+          if (cs[kk] != (Tc)0) {
+            row_load<LANES, CH>(R + (int64_t)ey * ld, ld, lane, v0[kk]);
+          } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[c][k] = u[c][k] - mm.mo * v[c][k];
-      if (mm.c > (Tc)2.5) {  // q = inf: diag(s != 0) - s s^T
-        Tc sv[CH][4];
-        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, sv);
-        Tc s = (Tc)0;
+            for (int c = 0; c < CH; ++c)
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+              for (int k = 0; k < 4; ++k) v0[kk][c][k] = (Tc)0;
+          }
+          if (cs[kk] < (Tc)0 || cs[kk] > (Tc)1.5) {
+            row_load<LANES, CH>(Yh + (int64_t)ex * ld, ld, lane, yh[kk]);
+          } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) s += sv[c][k] * v[c][k];
-        s = group_sum<LANES>(s, mask);
+            for (int c = 0; c < CH; ++c)
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+              for (int k = 0; k < 4; ++k) yh[kk][c][k] = (Tc)0;
+          }
+        }
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            accv[c][k] += (sv[c][k] != (Tc)0 ? v[c][k] : (Tc)0) - s * sv[c][k];
-      } else if (mm.c > (Tc)1.5) {  // q = 1: diagonal mask
-        Tc mk[CH][4];
-        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, mk);
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) accv[c][k] += mk[c][k] * v[c][k];
-      } else if (mm.c < (Tc)0) {
-        Tc yh[CH][4];
-        row_load<LANES, CH>(Yh + (int64_t)eo.x * ld, ld, lane, yh);
-        Tc s = (Tc)0;
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) s += yh[c][k] * v[c][k];
-        s = group_sum<LANES>(s, mask);
-        const Tc a = -mm.c;
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) accv[c][k] += a * (v[c][k] - s * yh[c][k]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) accv[c][k] += v[c][k];
+        for (int kk = 0; kk < NB; ++kk)
+          matvec_term<LANES, CH, Tc>(cs[kk], mos[kk], u, v0[kk], yh[kk], accv, mask);
       }
     }
-    Tc dot = (Tc)0;
     const Tc di = Dg ? Dg[i] : (Tc)1;  // diagonal term (1 for V; cluster sizes for the adjoint)
 #pragma unroll
     for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         accv[c][k] = di * u[c][k] + sg * accv[c][k];
-        dot += u[c][k] * accv[c][k];
+        dot_acc(dot, dot_e, u[c][k], accv[c][k]);
       }
-    acc[0] += (double)dot;
     row_store<LANES, CH>(W + i * ld, ld, lane, accv);
   }
+  double acc[1] = {(double)dot + (double)dot_e};
   double tot[1];
   if (grid_reduce<1>(acc, partials, &ctl->counter[C_MV], tot) && threadIdx.x == 0)
     cg_set_alpha(ctl, tot[0]);
@@ -534,8 +638,10 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
     sb = group_sum<LANES>(sb, mask);
     sv = group_sum<LANES>(sv, mask);
     ss = group_sum<LANES>(ss, mask);
-    const double nv = sqrt(sv);
-    const double shrink = (nv > r) ? 1.0 - r / nv : 0.0;
+    // norms and their inverses from refined inverse square roots (zero rows: 0)
+    const double rv = sv > 0.0 ? rsqrt_refined(sv) : 0.0;
+    const double nv = sv * rv;
+    const double shrink = (nv > r) ? 1.0 - r * rv : 0.0;
     double sres = 0.0;
 #pragma unroll
     for (int c = 0; c < CH; ++c)
@@ -545,7 +651,8 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
         sres = fma(res, res, sres);
       }
     acc[0] += sres;
-    const double ny = sqrt(ss);
+    const double rs = ss > 0.0 ? rsqrt_refined(ss) : 0.0;
+    const double ny = ss * rs;
     uint8_t kd;
     double scale, a;
     if (!(r > 0.0)) {
@@ -553,10 +660,10 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
     } else if (ny <= r) {
       kd = K_IN; scale = 1.0; a = 1.0;
     } else {
-      kd = K_OUT; scale = r / ny; a = r / ny;
+      kd = K_OUT; scale = r * rs; a = scale;
     }
     if (lane == 0) {
-      acc[1] += r * sqrt(sb);
+      acc[1] += sb > 0.0 ? r * (sb * rsqrt_refined(sb)) : 0.0;
       acc[2] += (ny <= r) ? 0.5 * ss : r * ny - 0.5 * r * r;
       acc[3] += (kd == K_OUT) ? 1.0 : 0.0;
       kind[e] = kd;
@@ -572,7 +679,7 @@ k_kkt_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
       row_store<LANES, CH>(Ut + e * ld, ld, lane, u);
     }
     if (kd == K_OUT) {
-      const Tc invc = (Tc)(1.0 / ny);
+      const Tc invc = to_operator<Tc>(rs);
       Tc yh[CH][4];
 #pragma unroll
       for (int c = 0; c < CH; ++c)

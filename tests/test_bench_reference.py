@@ -19,6 +19,10 @@ def test_reference_arm_json_line():
     for key in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "config"):
         assert key in d, key
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
-    assert d["cpu_baseline"]["cores"] >= 1 and "first 24 of 50 gammas" in d["cpu_baseline"]["sample"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    # the default workload's sample: 3,000 points of its recipe, every gamma of its grid
+    assert d["config"]["workload"] == "gmm200k_d50"
+    assert "n=3000 points" in d["cpu_baseline"]["sample"]
+    assert "first 30 of 30 gammas" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}

@@ -97,3 +97,35 @@ def test_batched_rejects_bad_problem(ccm):
     bad["edges"] = E
     with pytest.raises(ccm.CCMError):
         ccm.solve_path_batched([_dev(*probs[0]), bad], [0.1])
+
+
+def test_batched_config_sized_problems(ccm):
+    """Eight problems of the batched workload itself (n ~ U{500..5000}, d = 16,
+    2-20 components, k ~ U{5..15}, phi = 1/median, 25 gammas): the batched X
+    within 1e-6 relative of ccm_solve_path on the grid engine, whose (X, U) the
+    oracle checks for KKT and relative gap (Sec. 4) <= 1e-6; labels of both
+    equal to the oracle's labelling rule applied to the batched X."""
+    probs = synth.batched_problems(0, count=8)
+    assert min(p["A"].shape[0] for p in probs) >= 500
+    gam = probs[0]["gammas"]
+    dev = []
+    for p in probs:
+        A = torch.tensor(p["A"], device="cuda:0")
+        E, w, _ = ccm.build_graph(A, p["k"], p["phi"])
+        dev.append(dict(A=A, edges=E, w=w))
+    Xs, Ls, stats = ccm.solve_path_batched(dev, gam, tol=SOLVE_TOL)
+    for p, P, Xb, Lb, st in zip(probs, dev, Xs, Ls, stats):
+        Xg, Lg, Ug, stg = ccm.solve_path(P["A"], P["edges"], P["w"], gam, tol=SOLVE_TOL,
+                                         return_U=True, engine=1)
+        E = P["edges"].cpu().numpy().astype(np.int64)
+        w = P["w"].cpu().numpy()
+        for t, g in enumerate(gam):
+            assert st[t]["status"] == 0 and stg[t]["status"] == 0, (st[t], stg[t])
+            assert st[t]["kkt"] <= TOL and st[t]["gap"] <= TOL
+            xg = Xg[t].cpu().numpy()
+            res = okkt.kkt(p["A"], E, w, g, xg, Ug[t].cpu().numpy())
+            assert res["kkt"] <= TOL and res["gap"] <= TOL, (t, res)
+            xb = Xb[t].cpu().numpy()
+            assert np.linalg.norm(xb - xg) <= TOL * np.linalg.norm(xg), t
+            lab = olabels.labels(xb, E)
+            assert np.array_equal(Lb[t].cpu().numpy(), lab)

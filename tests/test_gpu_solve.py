@@ -222,3 +222,56 @@ def test_ring_kernels_after_another_solver_in_a_fresh_process(ccm):
     r = subprocess.run([sys.executable, "-c", _SHARED_KERNEL_SCRIPT], cwd=root,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_iteration_cap_reports_not_converged_with_outputs(ccm, engine):
+    """max_outer = 1 cannot reach the tolerance: the call returns
+    CCM_ERR_NOT_CONVERGED (status 5), every gamma's status says so, and X, the
+    labels and the statistics are still written (X finite, labels equal to the
+    oracle's rule on that X, KKT reported above the tolerance)."""
+    A, _, wl = synth.make_workload("gmm200_d2", 0)
+    E, w, _ = ograph.build_graph(A, wl.k, wl.phi)
+    g = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, 6)
+    At, Et, wt = _to_dev(A, E, w)
+    with pytest.raises(ccm.CCMError) as ei:
+        ccm.solve_path(At, Et, wt, g, tol=1e-12, engine=engine, max_outer=1, raise_on_cap=True)
+    assert ei.value.status == 5
+    X, lab, _, st = ccm.solve_path(At, Et, wt, g, tol=1e-12, engine=engine, max_outer=1)
+    X = X.cpu().numpy()
+    lab = lab.cpu().numpy()
+    assert np.all(np.isfinite(X))
+    assert any(s["status"] == 5 for s in st)
+    for t in range(len(g)):
+        assert st[t]["status"] in (0, 5) and st[t]["outer"] == 1
+        assert (st[t]["status"] == 0) == (st[t]["kkt"] <= 1e-12 and st[t]["gap"] <= 1e-12)
+        assert np.array_equal(lab[t], olabels.labels(X[t], E))
+
+
+def test_resume_from_saved_state_equals_full_path(ccm):
+    """Checkpoint / resume: solve gamma[:k], save (X, U) of gamma[k-1], then
+    solve gamma[k:] from X0 = X, U0 = U (a warm start, which also sends AUTO to
+    the grid engine). Both halves equal the uninterrupted path within 1e-6
+    relative; the solution of each gamma is unique (strongly convex model,
+    Sec. 1), only the iterates differ."""
+    A, _, wl = synth.make_workload("gmm200_d2", 1)
+    E, w, _ = ograph.build_graph(A, wl.k, wl.phi)
+    g = synth.gamma_grid(wl.gamma_lo, wl.gamma_hi, wl.n_gamma)
+    At, Et, wt = _to_dev(A, E, w)
+    Xf, Lf, _, _ = ccm.solve_path(At, Et, wt, g, tol=SOLVE_TOL)
+    k = 9
+    X1, L1, U1, _ = ccm.solve_path(At, Et, wt, g[:k], tol=SOLVE_TOL, return_U=True)
+    X2, L2, _, st2 = ccm.solve_path(At, Et, wt, g[k:], tol=SOLVE_TOL, X0=X1[-1].contiguous(),
+                                    U0=U1[-1].contiguous())
+    assert all(s["status"] == 0 for s in st2)
+    Xr = torch.cat([X1, X2]).cpu().numpy()
+    Xf = Xf.cpu().numpy()
+    for t in range(len(g)):
+        assert np.linalg.norm(Xr[t] - Xf[t]) <= TOL * np.linalg.norm(Xf[t]), t
+    Lr = torch.cat([L1, L2]).cpu().numpy()
+    Lf = Lf.cpu().numpy()
+    for t in range(len(g)):
+        if not _ambiguous(Xf[t], E):
+            assert np.array_equal(Lr[t], Lf[t]), t
+    with pytest.raises(ccm.CCMError):
+        ccm.solve_path(At, Et, wt, g[k:], tol=SOLVE_TOL, X0=X1[-1].contiguous(), engine=2)
