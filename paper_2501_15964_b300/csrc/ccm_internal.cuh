@@ -45,7 +45,7 @@ enum Slot : int {
   S_U, S_UT, S_YH, S_ALPHA, S_KIND, S_EDGES, S_CSR_OFF, S_CSR_INC, S_PART, S_CTRL,
   S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
   S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3, S_META, S_WPART, S_VJPF, S_ADMM,
-  S_COUNT
+  S_XF0, S_XF1, S_COUNT
 };
 
 struct Ctx {

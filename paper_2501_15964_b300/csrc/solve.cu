@@ -11,10 +11,44 @@
 
 #include "ccm_internal.cuh"
 #include "solve_common.cuh"
+#include "ff_kernels.cuh"
 #include "ring_kernels.cuh"
 #include "ssnal_kernels.cuh"
 
 namespace ccm {
+
+__global__ void k_pad_rows_ff(const double* __restrict__ src, float2* __restrict__ dst,
+                              int64_t rows, int d, int ld) {
+  const int64_t total = rows * ld;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / ld;
+    const int k = (int)(q - r * ld);
+    const ff f = (k < d) ? d2ff(src[r * d + k]) : ff{0.0f, 0.0f};
+    dst[q] = make_float2(f.h, f.l);
+  }
+}
+
+__global__ void k_unpad_rows_ff(const float2* __restrict__ src, double* __restrict__ dst,
+                                int64_t rows, int d, int ld) {
+  const int64_t total = rows * d;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / d;
+    const int k = (int)(q - r * d);
+    const float2 v = src[r * ld + k];
+    dst[q] = ff2d(ff{v.x, v.y});
+  }
+}
+
+__global__ void k_mirror_ff(const double* __restrict__ src, float2* __restrict__ dst,
+                            int64_t total) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const ff f = d2ff(src[q]);
+    dst[q] = make_float2(f.h, f.l);
+  }
+}
 
 __global__ void __launch_bounds__(256)
 k_kkt_node(const double* __restrict__ X, const double* __restrict__ Ap,
@@ -267,6 +301,15 @@ struct GridEngine {
     CCM_TRY(get(S_MINV, n * sizeof(Tc), &p)); Tc* Minv = (Tc*)p;
     CCM_TRY(get(S_U, std::max<int64_t>(ml, 1) * 8, &p)); double* Ua = (double*)p;
     CCM_TRY(get(S_UT, std::max<int64_t>(ml, 1) * 8, &p)); double* Ub = (double*)p;
+    // q = 2 with the float32 operator: the edge passes and the node gradient run
+    // in float-float (ff_kernels.cuh); U / Pi(y) rows are then float-float rows
+    // (same 8 bytes per element) and X has a float-float mirror
+    const bool FF = a.q == 2 && sizeof(Tc) == 4;
+    float2 *XFa = nullptr, *XFb = nullptr;
+    if (FF) {
+      CCM_TRY(get(S_XF0, nl * 8, &p)); XFa = (float2*)p;
+      CCM_TRY(get(S_XF1, nl * 8, &p)); XFb = (float2*)p;
+    }
     CCM_TRY(get(S_YH, std::max<int64_t>(ml, 1) * sizeof(Tc), &p)); Tc* Yh = (Tc*)p;
     CCM_TRY(get(S_ALPHA, std::max<int64_t>(m, 1) * sizeof(Tc), &p)); Tc* alpha = (Tc*)p;
     CCM_TRY(get(S_KIND, std::max<int64_t>(m, 1), &p)); uint8_t* kind = (uint8_t*)p;
@@ -290,8 +333,16 @@ struct GridEngine {
     CCM_COUNT(c);
     k_pad_rows<<<b_elem, threads, 0, s>>>(a.X0 ? a.X0 : a.A, Xa, n, d, ld);
     CCM_COUNT(c);
+    if (FF) {
+      k_mirror_ff<<<b_elem, threads, 0, s>>>(Xa, XFa, nl);
+      CCM_COUNT(c);
+      CCM_CUDA(cudaMemsetAsync(XFb, 0, nl * 8, s));
+    }
     if (m > 0) {
-      if (a.U0) {
+      if (a.U0 && FF) {
+        k_pad_rows_ff<<<nb(ml), threads, 0, s>>>(a.U0, (float2*)Ua, m, d, ld);
+        CCM_COUNT(c);
+      } else if (a.U0) {
         k_pad_rows<<<nb(ml), threads, 0, s>>>(a.U0, Ua, m, d, ld);
         CCM_COUNT(c);
       } else {
@@ -318,6 +369,8 @@ struct GridEngine {
     double* Xt = Xb;   // trial iterate
     double* U = Ua;    // current multipliers
     double* Ut = Ub;   // Pi(U + sigma B X) at the last evaluated point
+    float2* XF = XFa;  // float-float mirrors of X and Xt (FF only)
+    float2* XFt = XFb;
     double sigma = a.opt.sigma0;
     const bool prof = a.opt.profile != 0;
     ccm_profile profile = {};
@@ -335,7 +388,22 @@ struct GridEngine {
     int any_fail = 0;
 
     // evaluate phi, grad phi, Pi(y), yhat, alpha at Xc (one edge pass + one node pass)
-    auto evaluate = [&](const double* Xc, double* phi, double* gn, double* nout) -> int {
+    auto evaluate = [&](const double* Xc, const float2* XFc, double* phi, double* gn,
+                        double* nout) -> int {
+      if (FF) {
+        k_edge_eval_ff<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
+            XFc, (const float2*)U, edges, a.w, gamma_cur, sigma, (float2*)Ut, Yh, alpha, kind, m,
+            ld, part, ctl);
+        CCM_COUNT(c);
+        CCM_TRY(launch_node_grad_ff<L, CH, Tc>(c, Xc, Ap, (const float2*)Ut, off, inc, alpha,
+                                               kind, sigma, d, G, Minv, rp, n, ld, part, ctl, s));
+        CCM_CUDA(cudaGetLastError());
+        CCM_TRY(readback());
+        *phi = hc->eval[1] + hc->eval[0] / sigma;
+        *gn = std::sqrt(hc->eval[2]);
+        if (nout) *nout = 0;
+        return CCM_OK;
+      }
       if (a.q == 1)
         k_edge_eval_qn<1, L, CH, Tc><<<b_edge, threads, 0, s>>>(
             Xc, U, edges, a.w, gamma_cur, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
@@ -372,14 +440,19 @@ struct GridEngine {
       for (int outer = 0; outer < a.opt.max_outer; ++outer) {
         const double eps_in = std::min(std::max(0.5 * a.tol, 0.1 * last_kkt), eps_gap);
         if (edge_ready && edge_sigma == sigma) {
-          CCM_TRY(launch_node_grad<L, CH, Tc>(c, X, Ap, Ut, off, inc, alpha, kind, sigma, d, G,
-                                              Minv, rp, n, ld, part, ctl, s));
+          if (FF)
+            CCM_TRY(launch_node_grad_ff<L, CH, Tc>(c, X, Ap, (const float2*)Ut, off, inc, alpha,
+                                                   kind, sigma, d, G, Minv, rp, n, ld, part, ctl,
+                                                   s));
+          else
+            CCM_TRY(launch_node_grad<L, CH, Tc>(c, X, Ap, Ut, off, inc, alpha, kind, sigma, d, G,
+                                                Minv, rp, n, ld, part, ctl, s));
           CCM_CUDA(cudaGetLastError());
           CCM_TRY(readback());
           phi = hc->eval[1] + hc->eval[0] / sigma;
           gn = std::sqrt(hc->eval[2]);
         } else {
-          CCM_TRY(evaluate(X, &phi, &gn, nullptr));
+          CCM_TRY(evaluate(X, XF, &phi, &gn, nullptr));
         }
         edge_ready = false;
         for (int it = 0; it < a.opt.max_newton; ++it) {
@@ -418,23 +491,29 @@ struct GridEngine {
           st.cg += hc->cg.it;
           // Armijo backtracking on phi along Dx
           double tstep = 1.0;
-          k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
-          CCM_COUNT(c);
+          auto trial = [&]() {
+            if (FF)
+              k_trial_ff<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, XFt, nl, part, ctl);
+            else
+              k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
+            CCM_COUNT(c);
+          };
+          trial();
           CCM_CUDA(cudaGetLastError());
           CCM_TRY(readback());
           const double gd = hc->dots[0];
           const double slack = 1e-14 * (1.0 + std::fabs(phi));
           double phit = 0, gnt = 0;
           for (;;) {
-            CCM_TRY(evaluate(Xt, &phit, &gnt, nullptr));
+            CCM_TRY(evaluate(Xt, XFt, &phit, &gnt, nullptr));
             st.line_search += 1;
             if (phit <= phi + 1e-4 * tstep * gd + slack || tstep < 1e-10) break;
             tstep *= 0.5;
-            k_trial<Tc><<<b_elem, threads, 0, s>>>(X, Dx, G, tstep, Xt, nl, part, ctl);
-            CCM_COUNT(c);
+            trial();
             CCM_CUDA(cudaGetLastError());
           }
           std::swap(X, Xt);
+          std::swap(XF, XFt);
           phi = phit;
           gn = gnt;
           st.newton += 1;
@@ -449,6 +528,10 @@ struct GridEngine {
         else if (a.q == kQInf)
           k_kkt_edge_eval_qn<kQInf, L, CH, Tc><<<b_edge, threads, 0, s>>>(
               X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
+        else if (FF)
+          k_kkt_edge_eval_ff<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
+              XF, (const float2*)U, edges, a.w, gamma, sigma, (float2*)Ut, Yh, alpha, kind, m, ld,
+              part, ctl);
         else
           k_kkt_edge_eval<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
               X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, ld, part, ctl);
@@ -500,7 +583,11 @@ struct GridEngine {
       k_unpad_rows<<<nb(n * d), threads, 0, s>>>(X, a.Xout + (int64_t)t * n * d, n, d, ld);
       CCM_COUNT(c);
       if (a.Uout && m > 0) {
-        k_unpad_rows<<<nb(m * d), threads, 0, s>>>(U, a.Uout + (int64_t)t * m * d, m, d, ld);
+        if (FF)
+          k_unpad_rows_ff<<<nb(m * d), threads, 0, s>>>((const float2*)U,
+                                                        a.Uout + (int64_t)t * m * d, m, d, ld);
+        else
+          k_unpad_rows<<<nb(m * d), threads, 0, s>>>(U, a.Uout + (int64_t)t * m * d, m, d, ld);
         CCM_COUNT(c);
       }
       CCM_CUDA(cudaGetLastError());
