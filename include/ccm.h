@@ -203,6 +203,16 @@ int ccm_solve_path_ama(ccm_ctx* ctx, const double* A, int64_t n, int32_t d,
 /* Profile of the last ccm_solve_path run with options.profile = 1 (host out). */
 int ccm_last_profile(ccm_ctx* ctx, ccm_profile* out);
 
+/* How the last ccm_build_graph on this context found its candidates. */
+typedef struct {
+  int32_t candidates;       /* 1: tensor-core TF32 Gram form (d <= 128), 0: float32
+                               direct-difference tiles on the CUDA cores */
+  int32_t per_row;          /* candidates kept per row before the float64 re-rank */
+  int64_t rows_exhaustive;  /* rows the error bound could not certify, searched
+                               exhaustively in float64 */
+} ccm_graph_info;
+int ccm_last_graph_info(ccm_ctx* ctx, ccm_graph_info* out);
+
 /*
  * ccm_labels - cluster labels of one solution X (n x d) on an edge list, with
  * the fusion rule of ccm_solve_path. labels: device n int32. *n_clusters (host)

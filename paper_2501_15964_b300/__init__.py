@@ -33,6 +33,7 @@ from .api import (  # noqa: F401
     solve_path_admm,
     solve_path_ama,
     last_profile,
+    last_graph_info,
     launch_count,
     CCMPath,
     default_context,

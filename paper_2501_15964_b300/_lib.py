@@ -50,6 +50,11 @@ class Profile(C.Structure):
                 ("matvec_bytes_total", C.c_double), ("kernel_launches", C.c_int64)]
 
 
+class GraphInfo(C.Structure):
+    _fields_ = [("candidates", C.c_int32), ("per_row", C.c_int32),
+                ("rows_exhaustive", C.c_int64)]
+
+
 class Problem(C.Structure):
     _fields_ = [("A", C.c_void_p), ("edges", C.c_void_p), ("w", C.c_void_p),
                 ("n", C.c_int64), ("m", C.c_int64), ("X", C.c_void_p), ("labels", C.c_void_p)]
@@ -74,6 +79,7 @@ _SIGS = {
                                      C.POINTER(C.c_double), C.c_int32, C.c_int32, C.c_double,
                                      C.POINTER(Options), _P, _P, _P, C.POINTER(Stats), _P]),
     "ccm_last_profile": (C.c_int, [_P, C.POINTER(Profile)]),
+    "ccm_last_graph_info": (C.c_int, [_P, C.POINTER(GraphInfo)]),
     "ccm_launch_count": (C.c_int64, [_P]),
     "ccm_labels": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, C.c_int64, _P,
                              C.POINTER(C.c_int32), _P]),

@@ -5,8 +5,8 @@ import ctypes as C
 
 import torch
 
-from ._lib import (Q_INF, CCMError, Context, Options, Problem, Profile, Stats, check,
-                   load_library)
+from ._lib import (Q_INF, CCMError, Context, GraphInfo, Options, Problem, Profile, Stats,
+                   check, load_library)
 
 _CTX: dict[int, Context] = {}
 
@@ -149,6 +149,16 @@ def last_profile(ctx: Context | None = None) -> dict:
     check(load_library().ccm_last_profile(ctx.handle, C.byref(p)))
     return {"matvec_launches": p.matvec_launches, "matvec_ms_total": p.matvec_ms_total,
             "matvec_bytes_total": p.matvec_bytes_total, "kernel_launches": p.kernel_launches}
+
+
+def last_graph_info(ctx: Context | None = None) -> dict:
+    """How the last build_graph on the context found its candidates (see
+    ccm_last_graph_info): {"candidates": "tensor" | "simt", "per_row", "rows_exhaustive"}."""
+    ctx = ctx or default_context()
+    g = GraphInfo()
+    check(load_library().ccm_last_graph_info(ctx.handle, C.byref(g)))
+    return {"candidates": "tensor" if g.candidates == 1 else "simt", "per_row": g.per_row,
+            "rows_exhaustive": g.rows_exhaustive}
 
 
 def launch_count(ctx: Context | None = None) -> int:

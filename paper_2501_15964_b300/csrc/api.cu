@@ -210,6 +210,15 @@ int ccm_last_profile(ccm_ctx* x, ccm_profile* out) {
   return CCM_OK;
 }
 
+int ccm_last_graph_info(ccm_ctx* x, ccm_graph_info* out) {
+  if (!x || !out) {
+    set_error("ccm_last_graph_info: NULL argument");
+    return CCM_ERR_INVALID_ARG;
+  }
+  *out = x->c.last_graph;
+  return CCM_OK;
+}
+
 }  // extern "C"
 
 namespace ccm {

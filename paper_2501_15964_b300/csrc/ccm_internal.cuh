@@ -45,7 +45,7 @@ enum Slot : int {
   S_U, S_UT, S_YH, S_ALPHA, S_KIND, S_EDGES, S_CSR_OFF, S_CSR_INC, S_PART, S_CTRL,
   S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
   S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3, S_META, S_WPART, S_VJPF, S_ADMM,
-  S_XF0, S_XF1, S_COUNT
+  S_XF0, S_XF1, S_KNN, S_COUNT
 };
 
 struct Ctx {
@@ -58,6 +58,7 @@ struct Ctx {
   size_t host_pinned_size = 0;
   std::vector<cudaEvent_t> ev_pool;
   ccm_profile last_profile = {};
+  ccm_graph_info last_graph = {};
   int64_t launches = 0;          // kernels launched by this context (all calls)
   // dynamic shared-memory limit already raised per kernel, keyed by the kernel's
   // host address as seen by the launching translation unit (each .cu file holds
@@ -241,6 +242,12 @@ __device__ __forceinline__ bool grid_reduce(double (&acc)[NRED], double* partial
 // Cluster labels of X (row stride ldx) on an edge list (labels.cu).
 int labels_device(Ctx* c, const double* X, int64_t ldx, int64_t n, int d, const int2* edges,
                   int64_t m, int32_t* labels, int32_t* n_clusters, cudaStream_t s);
+
+// Tensor-core kNN candidates (knn_tc.cu): whether the kernel handles (d, K'),
+// and the candidate lists (n x *used_kp, *used_kp >= Kp) with their thresholds.
+int knn_tc_supported(int d, int Kp);
+int knn_candidates_tc(Ctx* c, const float* At, int ldf, int64_t n, int d, int Kp, int* cand,
+                      float* cand_thr, int* used_kp, cudaStream_t s);
 
 // Scan helpers (device-wide exclusive scan of int32 / int64).
 int scan_exclusive_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host,

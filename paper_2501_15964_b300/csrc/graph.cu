@@ -207,13 +207,24 @@ k_knn_tile(const float* __restrict__ At, int ldf, int64_t n, int Kp, int* __rest
 }
 
 // Canonical rerank of the K' candidates of each row; certify or flag.
+// tc_steps = 0: the candidates come from k_knn_tile (float32 direct differences,
+// the bound in the header comment). tc_steps > 0: they come from the tensor-core
+// Gram form of knn_tc.cu with tc_steps tcgen05.mma accumulation steps along K;
+// with b the float32 centred rows, n_i = ||b_i||^2, N = max n_j, u_k = 2^-k:
+//   E_G = 4 (u22 + S u22) sqrt(n_i N) + u21 (n_i + N)     (split remainder l l,
+//         float32 accumulation, float32 norms and the final combination),
+//   delta = u22 (sqrt(n_i) + sqrt(N))                    (|b' - (A - mu)| per row),
+//   E_R = 2 (sqrt(D~ + E_G) + delta) delta + delta^2     (from ||b'_i - b'_j|| to ||a_i - a_j||),
+//   E = (E_G + E_R)(1 + 1e-6) + d 2^-50 (D~ + E_G + E_R)  (canonical float64 rounding),
+// and the row is certified if D~_(K') - E(D~_(K')) > D_(k).
 __global__ void k_rerank(const double* __restrict__ A, int64_t n, int d, int k, int Kp,
                          const int* __restrict__ cand, const float* __restrict__ cand_thr,
                          const double* __restrict__ nrm, const double* __restrict__ nmax_p,
-                         int* __restrict__ nbr, int* __restrict__ flag) {
+                         int tc_steps, int* __restrict__ nbr, int* __restrict__ flag) {
   const double u = 5.9604644775390625e-08;  // 2^-24
   const double up = u * (1.0 + 2.0 * u);
   const double gd = d * u / (1.0 - d * u);
+  const double u22 = 2.384185791015625e-07, u21 = 4.76837158203125e-07;  // 2^-22, 2^-21
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double dl[KMAX];
@@ -235,8 +246,17 @@ __global__ void k_rerank(const double* __restrict__ A, int64_t n, int d, int k, 
     bool ok = cnt >= k;
     if (ok && cnt == Kp && (int64_t)Kp < n - 1) {
       const double thr = (double)cand_thr[i];
-      const double E = 2.0 * (gd * thr / (1.0 - gd) + 8.0 * up * (1.0 + up) *
-                                                          (nrm[i] + *nmax_p) * (1.0 + 1e-12));
+      double E;
+      if (tc_steps > 0) {
+        const double ni = nrm[i], N = *nmax_p;
+        const double EG = 4.0 * (u22 + tc_steps * u22) * sqrt(ni * N) + u21 * (ni + N);
+        const double dl_ = u22 * (sqrt(ni) + sqrt(N));
+        const double ER = 2.0 * (sqrt(fmax(thr, 0.0) + EG) + dl_) * dl_ + dl_ * dl_;
+        E = (EG + ER) * (1.0 + 1e-6) + d * 8.881784197001252e-16 * (fmax(thr, 0.0) + EG + ER);
+      } else {
+        E = 2.0 * (gd * thr / (1.0 - gd) +
+                   8.0 * up * (1.0 + up) * (nrm[i] + *nmax_p) * (1.0 + 1e-12));
+      }
       ok = (thr - E) > dl[k - 1];
     }
     for (int t = 0; t < k; ++t) nbr[i * k + t] = ok ? jl[t] : -1;
@@ -446,17 +466,31 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   k_max_nrm<<<1, 256, 0, s>>>(nrm, n, nmax);
   CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
-  // 2. candidates
-  CCM_TRY(ws_get(c, S_X1, (size_t)n * Kp * 4, &p));
+  // 2. candidates: tensor cores (d <= 128), else float32 SIMT tiles
+  CCM_TRY(ws_get(c, S_X1, (size_t)n * KMAX * 4, &p));
   int* cand = (int*)p;
   CCM_TRY(ws_get(c, S_G, (size_t)n * 4, &p));
   float* cthr = (float*)p;
-  size_t smem = sizeof(TileSmem);
-  CCM_CUDA(cudaFuncSetAttribute(k_knn_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
-  k_knn_tile<<<(unsigned)(n_pad / TR), threads, smem, s>>>(At, ldf, n, Kp, cand, cthr);
-  CCM_COUNT(c);
-  CCM_CUDA(cudaGetLastError());
+  int tc_steps = 0;
+  int Kc = Kp;  // candidates per row actually produced
+  if (knn_tc_supported(d, Kp)) {
+    int used = 0;
+    const int st = knn_candidates_tc(c, At, ldf, n, d, Kp, cand, cthr, &used, s);
+    if (st == CCM_OK) {
+      Kc = (int)std::min<int64_t>(used, KMAX);
+      tc_steps = 3 * (int)(round_up(d, 32) / 8);
+    } else if (st != CCM_ERR_TIMEOUT && st != CCM_ERR_UNSUPPORTED) {
+      return st;
+    }
+  }
+  if (tc_steps == 0) {
+    size_t smem = sizeof(TileSmem);
+    CCM_CUDA(cudaFuncSetAttribute(k_knn_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    k_knn_tile<<<(unsigned)(n_pad / TR), threads, smem, s>>>(At, ldf, n, Kp, cand, cthr);
+    CCM_COUNT(c);
+    CCM_CUDA(cudaGetLastError());
+  }
   // 3. rerank
   CCM_TRY(ws_get(c, S_DX, (size_t)n * k * 4, &p));
   int* nbr = (int*)p;
@@ -464,7 +498,7 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   int* flag = (int*)p;
   int* rows = flag + n;
   int* nflag = rows + n;
-  k_rerank<<<nb(n), 128, 0, s>>>(A, n, d, k, Kp, cand, cthr, nrm, nmax, nbr, flag);
+  k_rerank<<<nb(n), 128, 0, s>>>(A, n, d, k, Kc, cand, cthr, nrm, nmax, tc_steps, nbr, flag);
   CCM_COUNT(c);
   CCM_CUDA(cudaGetLastError());
   if (force_exact)  // every row exhaustively (exercises the fallback path)
@@ -475,6 +509,9 @@ int build_graph_device(Ctx* c, const double* A, int64_t n, int d, int k, double 
   CCM_CUDA(cudaGetLastError());
   CCM_TRY(sync_read(c, nflag, 4, &hp, s));
   const int nrows = *(int*)hp;
+  c->last_graph.candidates = tc_steps > 0 ? 1 : 0;
+  c->last_graph.per_row = Kc;
+  c->last_graph.rows_exhaustive = nrows;
   if (nrows > 0) {
     const int fb = (int)std::min<int64_t>(nrows, std::max<int64_t>(1, ((int64_t)1 << 28) / (n * 8) ));
     const int blocks = std::max(1, std::min(fb, c->num_sms * 4));

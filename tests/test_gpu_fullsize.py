@@ -68,6 +68,10 @@ def test_large_gmm_full_size(ccm, name):
     A, _, wl = synth.make_workload(name, 0)
     At = torch.tensor(A, device="cuda:0")
     Et, wt, phi = ccm.build_graph(At, wl.k, wl.phi)
+    info = ccm.last_graph_info()
+    # tensor-core candidates, every row certified by the error bound (no exhaustive
+    # float64 search needed at this size)
+    assert info["candidates"] == "tensor" and info["rows_exhaustive"] == 0, info
     E = Et.cpu().numpy().astype(np.int64)
     w = wt.cpu().numpy()
     n = A.shape[0]

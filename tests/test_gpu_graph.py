@@ -46,6 +46,24 @@ def test_graph_matches_oracle(ccm, name, n, phi):
 def test_graph_mnist_like_subsample(ccm):
     A, _, wl = synth.make_workload("mnist10k_d784", 0, n=1000)
     _check(ccm, A, 10, 0.0)
+    assert ccm.last_graph_info()["candidates"] == "simt"   # d > 128: CUDA-core tiles
+
+
+@pytest.mark.parametrize("d", [1, 2, 7, 16, 31, 33, 50, 64, 100, 128])
+def test_tensor_core_candidates_match_oracle(ccm, d):
+    """d <= 128: candidates from the tcgen05 TF32 Gram form (three-product
+    split), re-ranked in float64 under its error bound; the edge set must be the
+    oracle's exactly, and the bound must certify (nearly) every row so that the
+    exhaustive fallback stays rare. n = 700 spans several 128-row tiles and a
+    ragged last tile."""
+    rng = np.random.default_rng(100 + d)
+    n = 700
+    cent = rng.normal(0, 3, size=(6, d))
+    A = cent[rng.integers(0, 6, n)] + rng.normal(size=(n, d))
+    _check(ccm, A, 10, 0.0)
+    info = ccm.last_graph_info()
+    assert info["candidates"] == "tensor" and info["per_row"] == 32, info
+    assert info["rows_exhaustive"] <= n // 100, info
 
 
 @pytest.mark.parametrize("k", [1, 3, 7, 15, 32])
