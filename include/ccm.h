@@ -70,6 +70,10 @@ typedef struct {
                              BLOCK return CCM_ERR_UNSUPPORTED). */
   int32_t profile;        /* 1: time every Newton-CG operator launch with CUDA events
                              (read back with ccm_last_profile) */
+  int32_t relabel;        /* 1 (default): the grid engine solves n >= 16384 with the
+                             nodes relabelled by connected component of the graph
+                             (better cache reuse of gathered rows; inputs and outputs
+                             keep the caller's order); 0: never */
   const double* X0;       /* optional device n x d warm start for the first gamma, or NULL */
   const double* U0;       /* optional device m x d multipliers for the first gamma (must
                              satisfy ||u_l|| <= gamma_1 w_l), or NULL */

@@ -29,6 +29,7 @@ class Options(C.Structure):
         ("sigma0", C.c_double), ("sigma_max", C.c_double),
         ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
         ("precision", C.c_int32), ("engine", C.c_int32), ("profile", C.c_int32),
+        ("relabel", C.c_int32),
         ("X0", C.c_void_p), ("U0", C.c_void_p),
     ]
 

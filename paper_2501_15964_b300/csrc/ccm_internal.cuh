@@ -45,7 +45,7 @@ enum Slot : int {
   S_U, S_UT, S_YH, S_ALPHA, S_KIND, S_EDGES, S_CSR_OFF, S_CSR_INC, S_PART, S_CTRL,
   S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
   S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3, S_META, S_WPART, S_VJPF, S_ADMM,
-  S_XF0, S_XF1, S_KNN, S_COUNT
+  S_XF0, S_XF1, S_KNN, S_REORD, S_COUNT
 };
 
 struct Ctx {
@@ -64,7 +64,25 @@ struct Ctx {
   // host address as seen by the launching translation unit (each .cu file holds
   // its own instance of a template kernel, so one kernel name can have several)
   std::vector<std::pair<const void*, size_t>> smem_attr;
+  // blocks resident on the whole GPU per kernel (occupancy x SMs), keyed like smem_attr
+  std::vector<std::pair<const void*, int>> resident;
 };
+
+// Blocks of `threads` threads (no dynamic shared memory) that kernel fn can keep
+// resident on every SM at once, times the SM count: a grid-stride kernel
+// launched with at most this many blocks runs in one wave.
+template <typename F>
+inline int resident_grid(Ctx* c, F fn, int threads) {
+  const void* key = (const void*)fn;
+  for (auto& e : c->resident)
+    if (e.first == key) return e.second;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0) != cudaSuccess)
+    per = 1;
+  per = per < 1 ? 1 : (per > 8 ? 8 : per);
+  c->resident.emplace_back(key, per * c->num_sms);
+  return per * c->num_sms;
+}
 
 // Count one kernel launch on context c (for launch statistics).
 #define CCM_COUNT(c) ((c)->launches++)
@@ -248,6 +266,20 @@ int labels_device(Ctx* c, const double* X, int64_t ldx, int64_t n, int d, const 
 int knn_tc_supported(int d, int Kp);
 int knn_candidates_tc(Ctx* c, const float* At, int ldf, int64_t n, int d, int Kp, int* cand,
                       float* cand_thr, int* used_kp, cudaStream_t s);
+
+// Node relabelling for locality (reorder.cu): perm maps new -> old node, iperm
+// old -> new; edges / w are the relabelled, oriented and sorted edge list and its
+// weights; eperm maps new -> old edge id, complemented (~id) where the endpoints
+// swapped (the edge's B X row changes sign). All device arrays in scratch.
+struct Relabel {
+  int* perm = nullptr;
+  int* iperm = nullptr;
+  int2* edges = nullptr;
+  double* w = nullptr;
+  int* eperm = nullptr;
+};
+int locality_relabel(Ctx* c, const int2* edges, const double* w, int64_t m, int64_t n,
+                     Relabel& r, cudaStream_t s);
 
 // Scan helpers (device-wide exclusive scan of int32 / int64).
 int scan_exclusive_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host,

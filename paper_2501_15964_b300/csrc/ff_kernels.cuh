@@ -17,12 +17,13 @@
 
 namespace ccm {
 
-// float64 rows (stride d) -> float-float rows (stride ld, zero padding)
+// float64 rows (stride d) -> float-float rows (stride ld, zero padding), row r
+// taken from source row idx[r] (negated when complemented; idx may be NULL)
 __global__ void k_pad_rows_ff(const double* __restrict__ src, float2* __restrict__ dst,
-                              int64_t rows, int d, int ld);
-// float-float rows (stride ld) -> float64 rows (stride d)
+                              int64_t rows, int d, int ld, const int* __restrict__ idx);
+// float-float rows (stride ld) -> float64 rows (stride d), row r stored to idx[r]
 __global__ void k_unpad_rows_ff(const float2* __restrict__ src, double* __restrict__ dst,
-                                int64_t rows, int d, int ld);
+                                int64_t rows, int d, int ld, const int* __restrict__ idx);
 // float64 rows (stride ld) -> their float-float mirror (same stride)
 __global__ void k_mirror_ff(const double* __restrict__ src, float2* __restrict__ dst,
                             int64_t total);
@@ -483,10 +484,11 @@ inline int launch_node_grad_ff(Ctx* c, const double* X, const double* Ap, const 
   } else {
     const int threads = 256;
     const int gpb = threads / L;
+    auto fn = k_node_grad_ff<L, CH, Tc>;
     const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
-    k_node_grad_ff<L, CH, Tc><<<blocks, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma,
-                                                         d, G, Minv, n, ld, part, ctl);
+        1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)resident_grid(c, fn, threads)));
+    fn<<<blocks, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv, n, ld,
+                                  part, ctl);
   }
   CCM_COUNT(c);
   return CCM_OK;

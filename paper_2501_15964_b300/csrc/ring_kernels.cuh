@@ -256,22 +256,23 @@ k_cg_matvec_ring(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc
           }
         }
       }
-      Tc dot = (Tc)0;
+      Tc dot = (Tc)0, dot_e = (Tc)0;  // <W_i, u_i> over this lane's elements, float-float
       const Tc di = Dg ? Dg[i] : (Tc)1;
 #pragma unroll
       for (int c = 0; c < CH; ++c)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           accv[c][k] = di * u[c][k] + sg * accv[c][k];
-          dot += u[c][k] * accv[c][k];
+          dot_acc(dot, dot_e, u[c][k], accv[c][k]);
         }
       row_store<LANES, CH>(W + (int64_t)i * ld, ld, lane, accv);
+      const double dnode = (double)dot + (double)dot_e;
       if (np > 1) {  // the split node's own reduction row
-        const double dsum = group_sum<LANES>((double)dot, 0xffffffffu);
+        const double dsum = group_sum<LANES>(dnode, 0xffffffffu);
         const int wf = i == sp.i0 ? sp.wf0 : sp.wf1;
         if (lane == 0) partials[(size_t)gridDim.x + wf] = dsum;
       } else {
-        acc[0] += (double)dot;
+        acc[0] += dnode;
       }
     }
     cp_async_wait<0>();
@@ -574,10 +575,11 @@ inline int launch_node_grad(Ctx* c, const double* X, const double* Ap, const dou
   } else {
     const int threads = 256;
     const int gpb = threads / L;
+    auto fn = k_node_grad<L, CH, Tc>;
     const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
-    k_node_grad<L, CH, Tc><<<blocks, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma, d,
-                                                      G, Minv, n, ld, part, ctl);
+        1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)resident_grid(c, fn, threads)));
+    fn<<<blocks, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv, n, ld,
+                                  part, ctl);
   }
   CCM_COUNT(c);
   return CCM_OK;

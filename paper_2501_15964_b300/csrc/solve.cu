@@ -17,27 +17,74 @@
 
 namespace ccm {
 
-__global__ void k_pad_rows_ff(const double* __restrict__ src, float2* __restrict__ dst,
-                              int64_t rows, int d, int ld) {
+// node count from which ccm_solve_path relabels nodes by graph component
+static constexpr int64_t kRelabelMinN = 16384;
+
+// Row gather into the padded layout / scatter back out of it. idx (optional)
+// maps a padded row to its source / destination row; a complemented entry (~r)
+// marks an edge whose endpoints swapped under the node relabelling, whose row
+// changes sign.
+__device__ __forceinline__ int64_t idx_row(const int* idx, int64_t r, double& sg) {
+  if (!idx) {
+    sg = 1.0;
+    return r;
+  }
+  const int v = idx[r];
+  sg = v < 0 ? -1.0 : 1.0;
+  return v < 0 ? (int64_t)~v : (int64_t)v;
+}
+
+__global__ void k_gather_rows(const double* __restrict__ src, double* __restrict__ dst,
+                              int64_t rows, int d, int ld, const int* __restrict__ idx) {
   const int64_t total = rows * ld;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = q / ld;
     const int k = (int)(q - r * ld);
-    const ff f = (k < d) ? d2ff(src[r * d + k]) : ff{0.0f, 0.0f};
-    dst[q] = make_float2(f.h, f.l);
+    double sg;
+    const int64_t rs = idx_row(idx, r, sg);
+    dst[q] = (k < d) ? sg * src[rs * d + k] : 0.0;
   }
 }
 
-__global__ void k_unpad_rows_ff(const float2* __restrict__ src, double* __restrict__ dst,
-                                int64_t rows, int d, int ld) {
+__global__ void k_scatter_rows(const double* __restrict__ src, double* __restrict__ dst,
+                               int64_t rows, int d, int ld, const int* __restrict__ idx) {
   const int64_t total = rows * d;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = q / d;
     const int k = (int)(q - r * d);
+    double sg;
+    const int64_t rd = idx_row(idx, r, sg);
+    dst[rd * d + k] = sg * src[r * ld + k];
+  }
+}
+
+__global__ void k_pad_rows_ff(const double* __restrict__ src, float2* __restrict__ dst,
+                              int64_t rows, int d, int ld, const int* __restrict__ idx) {
+  const int64_t total = rows * ld;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / ld;
+    const int k = (int)(q - r * ld);
+    double sg;
+    const int64_t rs = idx_row(idx, r, sg);
+    const ff f = (k < d) ? d2ff(sg * src[rs * d + k]) : ff{0.0f, 0.0f};
+    dst[q] = make_float2(f.h, f.l);
+  }
+}
+
+__global__ void k_unpad_rows_ff(const float2* __restrict__ src, double* __restrict__ dst,
+                                int64_t rows, int d, int ld, const int* __restrict__ idx) {
+  const int64_t total = rows * d;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / d;
+    const int k = (int)(q - r * d);
+    double sg;
+    const int64_t rd = idx_row(idx, r, sg);
     const float2 v = src[r * ld + k];
-    dst[q] = ff2d(ff{v.x, v.y});
+    dst[rd * d + k] = sg * ff2d(ff{v.x, v.y});
   }
 }
 
@@ -329,9 +376,9 @@ struct GridEngine {
     RingPlan rp;
     CCM_TRY(ring_plan<Tc>(c, L, ld, off, n, rp, s));
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
-    k_pad_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld);
+    k_gather_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld, a.perm);
     CCM_COUNT(c);
-    k_pad_rows<<<b_elem, threads, 0, s>>>(a.X0 ? a.X0 : a.A, Xa, n, d, ld);
+    k_gather_rows<<<b_elem, threads, 0, s>>>(a.X0 ? a.X0 : a.A, Xa, n, d, ld, a.perm);
     CCM_COUNT(c);
     if (FF) {
       k_mirror_ff<<<b_elem, threads, 0, s>>>(Xa, XFa, nl);
@@ -340,10 +387,10 @@ struct GridEngine {
     }
     if (m > 0) {
       if (a.U0 && FF) {
-        k_pad_rows_ff<<<nb(ml), threads, 0, s>>>(a.U0, (float2*)Ua, m, d, ld);
+        k_pad_rows_ff<<<nb(ml), threads, 0, s>>>(a.U0, (float2*)Ua, m, d, ld, a.eperm);
         CCM_COUNT(c);
       } else if (a.U0) {
-        k_pad_rows<<<nb(ml), threads, 0, s>>>(a.U0, Ua, m, d, ld);
+        k_gather_rows<<<nb(ml), threads, 0, s>>>(a.U0, Ua, m, d, ld, a.eperm);
         CCM_COUNT(c);
       } else {
         CCM_CUDA(cudaMemsetAsync(Ua, 0, ml * 8, s));
@@ -580,14 +627,17 @@ struct GridEngine {
       st.sigma = sigma;
       st.status = converged ? CCM_OK : CCM_ERR_NOT_CONVERGED;
       if (!converged) any_fail = 1;
-      k_unpad_rows<<<nb(n * d), threads, 0, s>>>(X, a.Xout + (int64_t)t * n * d, n, d, ld);
+      k_scatter_rows<<<nb(n * d), threads, 0, s>>>(X, a.Xout + (int64_t)t * n * d, n, d, ld,
+                                                   a.perm);
       CCM_COUNT(c);
       if (a.Uout && m > 0) {
         if (FF)
           k_unpad_rows_ff<<<nb(m * d), threads, 0, s>>>((const float2*)U,
-                                                        a.Uout + (int64_t)t * m * d, m, d, ld);
+                                                        a.Uout + (int64_t)t * m * d, m, d, ld,
+                                                        a.eperm);
         else
-          k_unpad_rows<<<nb(m * d), threads, 0, s>>>(U, a.Uout + (int64_t)t * m * d, m, d, ld);
+          k_scatter_rows<<<nb(m * d), threads, 0, s>>>(U, a.Uout + (int64_t)t * m * d, m, d, ld,
+                                                       a.eperm);
         CCM_COUNT(c);
       }
       CCM_CUDA(cudaGetLastError());
@@ -692,6 +742,16 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     c->last_profile.kernel_launches = c->launches - launches0;
     if (st == CCM_ERR_NOT_CONVERGED) set_error("ccm_solve_path: some gamma hit an iteration cap");
     return st;
+  }
+  // large graphs: solve with the nodes grouped by connected component (locality of
+  // the gathers); the engine reads and writes the caller's arrays through the maps
+  if (o.relabel && n >= kRelabelMinN && m > 0) {
+    Relabel r;
+    CCM_TRY(locality_relabel(c, (const int2*)edges, w, m, n, r, s));
+    a.edges = (const int32_t*)r.edges;
+    a.w = r.w;
+    a.perm = r.perm;
+    a.eperm = r.eperm;
   }
   int st = solve_grid(c, a, s);
   if (st != CCM_OK && st != CCM_ERR_NOT_CONVERGED) return st;

@@ -22,6 +22,11 @@ struct SolveArgs {
   const double* X0 = nullptr;
   const double* U0 = nullptr;
   int q = 2;  // norm of the differences: 2 (group lasso), 1 (elementwise) or CCM_Q_INF (max)
+  // node relabelling (grid engine; both NULL = identity): A, X0 rows are read
+  // through perm (new -> old) and X rows written back through it; U0 / U rows
+  // through eperm (new -> old edge, ~id = endpoints swapped: the row's sign flips)
+  const int* perm = nullptr;
+  const int* eperm = nullptr;
 
   // Algorithmic bytes of one Newton-CG operator launch (each datum once):
   // R read and W written (n x ld each), Minv (n), the yhat rows of the m_out

@@ -526,9 +526,10 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
   const Tc al = (Tc)ctl->cg.alpha;
   const Tc be = (Tc)ctl->cg.beta;
   const bool first = ctl->cg.it == 0;
-  // a thread's few quads are summed in Tc, then once in float64 (conversions and
-  // float64 additions occupy B300's narrow FP64 pipe)
-  Tc rz_t = (Tc)0, rr_t = (Tc)0;
+  // a thread's products are summed exactly enough in float-float (two-product and
+  // two-sum on the FP32 pipe; plain sums for float64 vectors), then once in
+  // float64: float64 arithmetic per element would occupy B300's narrow FP64 pipe
+  Tc rz_t = (Tc)0, rz_e = (Tc)0, rr_t = (Tc)0, rr_e = (Tc)0;
   const int64_t total = n * ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; t4 < total;
@@ -553,21 +554,19 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
         sv[k] = w[k] + be * sv[k];
       }
     }
-    Tc rr = (Tc)0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       dx[k] += al * p[k];
       r[k] -= al * sv[k];
-      rr += r[k] * r[k];
+      dot_acc(rr_t, rr_e, r[k], r[k]);
+      dot_acc(rz_t, rz_e, mi * r[k], r[k]);
     }
     Vec4<Tc>::store(Dx + t4, dx);
     Vec4<Tc>::store(P + t4, p);
     Vec4<Tc>::store(S + t4, sv);
     Vec4<Tc>::store(R + t4, r);
-    rz_t += mi * rr;
-    rr_t += rr;
   }
-  double acc[2] = {(double)rz_t, (double)rr_t};
+  double acc[2] = {(double)rz_t + (double)rz_e, (double)rr_t + (double)rr_e};
   double tot[2];
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_UPD], tot) && threadIdx.x == 0) {
     CgCtl& c = ctl->cg;
@@ -1001,10 +1000,10 @@ inline int launch_matvec_reg(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, 
                              Ctl* ctl, cudaStream_t s) {
   const int threads = 256;
   const int gpb = threads / L;
-  const int blocks =
-      (int)std::max<int64_t>(1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)c->num_sms * 4));
-  k_cg_matvec<L, CH, Tc><<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma, n,
-                                                    ld, part, ctl);
+  auto fn = k_cg_matvec<L, CH, Tc>;
+  const int blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)resident_grid(c, fn, threads)));
+  fn<<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma, n, ld, part, ctl);
   CCM_COUNT(c);
   return CCM_OK;
 }

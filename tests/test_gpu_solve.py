@@ -275,3 +275,46 @@ def test_resume_from_saved_state_equals_full_path(ccm):
             assert np.array_equal(Lr[t], Lf[t]), t
     with pytest.raises(ccm.CCMError):
         ccm.solve_path(At, Et, wt, g[k:], tol=SOLVE_TOL, X0=X1[-1].contiguous(), engine=2)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_relabelled_solve_matches_plain_order(ccm, precision):
+    """From n = 16,384 nodes the grid engine solves with the nodes grouped by
+    connected component (options.relabel = 1, the default) and maps inputs and
+    outputs through the permutation, flipping the sign of U rows whose edge
+    endpoints swap. The solution is unique (Sec. 1), so X must agree with the
+    solve in the caller's order; the oracle's KKT residuals and gap of the
+    returned (X, U) check the U rows and their signs; labels agree where no
+    edge distance is in the ambiguous band."""
+    rng = np.random.default_rng(17)
+    n, d = 20000, 3
+    cent = rng.normal(0, 4, size=(40, d))
+    A = cent[rng.integers(0, 40, n)] + 0.7 * rng.normal(size=(n, d))
+    At = torch.tensor(A, device="cuda:0")
+    Et, wt, _ = ccm.build_graph(At, 6, 0.0)
+    E = Et.cpu().numpy().astype(np.int64)
+    w = wt.cpu().numpy()
+    g = [0.01, 0.1, 0.6]
+    runs = {}
+    for rl in (0, 1):
+        X, L, U, st = ccm.solve_path(At, Et, wt, g, tol=SOLVE_TOL, return_U=True,
+                                     precision=precision, relabel=rl)
+        assert all(s["status"] == 0 for s in st)
+        runs[rl] = (X.cpu().numpy(), L.cpu().numpy(), U.cpu().numpy())
+    for t, gm in enumerate(g):
+        X0, L0, _ = runs[0]
+        X1, L1, U1 = runs[1]
+        assert np.linalg.norm(X1[t] - X0[t]) <= TOL * np.linalg.norm(X0[t]), t
+        res = okkt.kkt(A, E, w, gm, X1[t], U1[t])
+        assert res["kkt"] <= TOL and res["gap"] <= TOL, (t, res)
+        assert np.array_equal(L1[t], olabels.labels(X1[t], E))
+        if not _ambiguous(X0[t], E):
+            assert np.array_equal(L1[t], L0[t]), t
+    # warm start through the maps: U0 rows enter with their signs
+    Xa, _, Ua, _ = ccm.solve_path(At, Et, wt, g[:2], tol=SOLVE_TOL, return_U=True,
+                                  precision=precision)
+    Xb, _, _, stb = ccm.solve_path(At, Et, wt, g[2:], tol=SOLVE_TOL, precision=precision,
+                                   X0=Xa[-1].contiguous(), U0=Ua[-1].contiguous())
+    assert stb[0]["status"] == 0
+    Xb = Xb.cpu().numpy()
+    assert np.linalg.norm(Xb[0] - runs[0][0][2]) <= TOL * np.linalg.norm(runs[0][0][2])
