@@ -228,9 +228,12 @@ def form_batched(args):
     flat = [s for ps in st for s in ps]
     nloop = min(args.loop, len(dev))
 
-    def loop():
+    shape = ccm.last_profile()
+    shape = {"lanes": shape["block_lanes"], "quads_per_lane": shape["block_quads"]}
+
+    def loop():  # each problem with the engine ccm_solve_path picks by itself (AUTO)
         for p in dev[:nloop]:
-            ccm.solve_path(p["A"], p["edges"], p["w"], gam, tol=SOLVE_TOL, engine=1)
+            ccm.solve_path(p["A"], p["edges"], p["w"], gam, tol=SOLVE_TOL, engine=0)
     loop()
     ms_l, _ = _time(loop, stream, 1)
     ms_sub, _ = _time(lambda: ccm.solve_path_batched(dev[:nloop], gam, tol=SOLVE_TOL), stream, 1)
@@ -239,7 +242,7 @@ def form_batched(args):
             "batched_value": len(dev) * T / (ms_b / 1000), "batched_ms": ms_b,
             "loop_problems": nloop, "loop_value": nloop * T / (ms_l / 1000), "loop_ms": ms_l,
             "batched_same_subset_value": nloop * T / (ms_sub / 1000),
-            "speedup_same_subset": ms_l / ms_sub,
+            "speedup_same_subset": ms_l / ms_sub, "autotuned_shape": shape,
             "max_kkt": max(s["kkt"] for s in flat), "max_gap": max(s["gap"] for s in flat),
             "not_converged": sum(1 for s in flat if s["status"] != 0)}
     print(json.dumps(line), flush=True)

@@ -43,7 +43,9 @@ typedef enum {
   CCM_ERR_OOM = 4,              /* scratch allocation failed */
   CCM_ERR_NOT_CONVERGED = 5,    /* an iteration cap was hit; outputs are still written */
   CCM_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
-  CCM_ERR_BUFFER_TOO_SMALL = 7  /* an output capacity is too small; *m_out says how much */
+  CCM_ERR_BUFFER_TOO_SMALL = 7, /* an output capacity is too small; *m_out says how much */
+  CCM_ERR_BOUNDS = 8            /* bounds-checked build only (CCM_DEBUG_BOUNDS): a kernel met
+                                   an out-of-range index, skipped the access and recorded it */
 } ccm_status;
 
 /* The value of the int32 argument q that selects q = inf (the max norm). */
@@ -74,6 +76,10 @@ typedef struct {
                              nodes relabelled by connected component of the graph
                              (better cache reuse of gathered rows; inputs and outputs
                              keep the caller's order); 0: never */
+  int32_t autotune;       /* 1 (default): ccm_solve_path_batched measures its group
+                             shapes (lanes x quads per row) on a sample of a batch of
+                             >= 8 problems and caches the fastest per context, d,
+                             precision and mean degree; 0: default shape unless cached */
   const double* X0;       /* optional device n x d warm start for the first gamma, or NULL */
   const double* U0;       /* optional device m x d multipliers for the first gamma (must
                              satisfy ||u_l|| <= gamma_1 w_l), or NULL */
@@ -99,6 +105,8 @@ typedef struct {
   double matvec_ms_total;
   double matvec_bytes_total; /* algorithmic bytes moved by those launches */
   int64_t kernel_launches;   /* all kernels the last ccm_solve_path call launched */
+  int32_t block_lanes;       /* block engine (last block-engine call): lanes per row group */
+  int32_t block_quads;       /* ... and quads per lane (the autotuned or cached shape) */
 } ccm_profile;
 
 /* Total number of kernels launched through this context since ccm_create. */

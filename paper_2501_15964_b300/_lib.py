@@ -14,7 +14,7 @@ ENGINE_AUTO, ENGINE_GRID, ENGINE_BLOCK = 0, 1, 2
 STATUS = {
     0: "CCM_OK", 1: "CCM_ERR_INVALID_ARG", 2: "CCM_ERR_UNSUPPORTED", 3: "CCM_ERR_CUDA",
     4: "CCM_ERR_OOM", 5: "CCM_ERR_NOT_CONVERGED", 6: "CCM_ERR_TIMEOUT",
-    7: "CCM_ERR_BUFFER_TOO_SMALL",
+    7: "CCM_ERR_BUFFER_TOO_SMALL", 8: "CCM_ERR_BOUNDS",
 }
 
 
@@ -29,7 +29,7 @@ class Options(C.Structure):
         ("sigma0", C.c_double), ("sigma_max", C.c_double),
         ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
         ("precision", C.c_int32), ("engine", C.c_int32), ("profile", C.c_int32),
-        ("relabel", C.c_int32),
+        ("relabel", C.c_int32), ("autotune", C.c_int32),
         ("X0", C.c_void_p), ("U0", C.c_void_p),
     ]
 
@@ -48,7 +48,8 @@ class Stats(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("matvec_launches", C.c_int64), ("matvec_ms_total", C.c_double),
-                ("matvec_bytes_total", C.c_double), ("kernel_launches", C.c_int64)]
+                ("matvec_bytes_total", C.c_double), ("kernel_launches", C.c_int64),
+                ("block_lanes", C.c_int32), ("block_quads", C.c_int32)]
 
 
 class GraphInfo(C.Structure):
@@ -93,7 +94,15 @@ _SIGS = {
 
 
 def lib_path() -> str:
-    return os.path.join(HERE, "libccm.so")
+    """The library to load: libccm.so next to this file, or the file named by the
+    CCM_LIBRARY environment variable (for example the bounds-checked build
+    libccm_debug.so)."""
+    return os.environ.get("CCM_LIBRARY") or os.path.join(HERE, "libccm.so")
+
+
+def debug_lib_path() -> str:
+    """The bounds-checked build (compiled with CCM_DEBUG_BOUNDS)."""
+    return os.path.join(HERE, "libccm_debug.so")
 
 
 def load_library():

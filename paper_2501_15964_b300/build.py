@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libccm.so")
 BUILD = os.path.join(HERE, "_build")
+# bounds-checked build: the same sources with CCM_DEBUG_BOUNDS (index checks that
+# record the first bad index and skip the access; see ssnal_kernels.cuh)
+OUT_DEBUG = os.path.join(HERE, "libccm_debug.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -33,11 +37,11 @@ def _needs(obj, src):
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def _compile(src, verbose=False):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, verbose=False, debug=False):
+    obj = os.path.join(BUILD_DEBUG if debug else BUILD, os.path.basename(src)[:-3] + ".o")
     if not _needs(obj, src):
         return obj, ""
-    cmd = ["nvcc", *ARCH, *FLAGS, "-c", src, "-o", obj]
+    cmd = ["nvcc", *ARCH, *FLAGS, *(["-DCCM_DEBUG_BOUNDS"] if debug else []), "-c", src, "-o", obj]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -46,23 +50,26 @@ def _compile(src, verbose=False):
     return obj, r.stderr
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile every .cu file and link libccm.so (debug=True: the bounds-checked
+    libccm_debug.so). Objects are rebuilt only when a source or header changed."""
+    out, bdir = (OUT_DEBUG, BUILD_DEBUG) if debug else (OUT, BUILD)
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 1)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose, debug), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    if (not os.path.exists(OUT)) or any(os.path.getmtime(o) > os.path.getmtime(OUT) for o in objs):
-        cmd = ["nvcc", *ARCH, "-shared", "-o", OUT, *objs, "-lcudart"]
+    if (not os.path.exists(out)) or any(os.path.getmtime(o) > os.path.getmtime(out) for o in objs):
+        cmd = ["nvcc", *ARCH, "-shared", "-o", out, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-    return OUT
+    return out
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

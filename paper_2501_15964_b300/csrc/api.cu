@@ -159,6 +159,7 @@ void ccm_default_options(ccm_options* o) {
   o->engine = CCM_ENGINE_AUTO;
   o->profile = 0;
   o->relabel = 1;
+  o->autotune = 1;
   o->X0 = nullptr;
   o->U0 = nullptr;
 }

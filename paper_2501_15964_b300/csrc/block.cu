@@ -772,19 +772,113 @@ static int run_block_engine(Ctx* c, const std::vector<HostProblem>& hp, int d, c
   return fail ? CCM_ERR_NOT_CONVERGED : CCM_OK;
 }
 
+// ---------------------------------------------------------------- shapes and autotuning
+// A row of nq quads is handled by a group of L lanes with CH quads each (L CH >=
+// nq): 32 / L edges (or nodes) per warp. The default takes the narrowest power of
+// two L >= nq with CH = 1; the alternatives fold it to L/2 x 2 and L/4 x 4, which
+// put more edges in flight per warp and shorten the group sums at the price of
+// registers per thread.
+template <typename Tc>
+static int run_shape(Ctx* c, int L, int CH, const std::vector<HostProblem>& hp, int d,
+                     const double* g, int T, double tol, const ccm_options& o, ccm_stats* st,
+                     cudaStream_t s) {
+#define CCM_SHAPE(LL, CC) \
+  if (L == LL && CH == CC) return run_block_engine<LL, CC, Tc>(c, hp, d, g, T, tol, o, st, s);
+  CCM_SHAPE(1, 1) CCM_SHAPE(2, 1) CCM_SHAPE(1, 2) CCM_SHAPE(4, 1) CCM_SHAPE(2, 2) CCM_SHAPE(1, 4)
+  CCM_SHAPE(8, 1) CCM_SHAPE(4, 2) CCM_SHAPE(2, 4) CCM_SHAPE(16, 1) CCM_SHAPE(8, 2)
+  CCM_SHAPE(4, 4) CCM_SHAPE(32, 1) CCM_SHAPE(16, 2) CCM_SHAPE(8, 4)
+#undef CCM_SHAPE
+  set_error("block engine: no kernel for %d lanes x %d quads", L, CH);
+  return CCM_ERR_UNSUPPORTED;
+}
+
+static int default_lanes(int d) {
+  const int nq = (int)(round_up(d, 4) / 4);
+  int L = 1;
+  while (L < nq) L <<= 1;
+  return L;
+}
+
+// Shape for a batch: the measured best of the candidates on a sample of the
+// batch, cached per context and (d, precision, mean-degree bucket). Tuning runs
+// when the batch has at least kTuneMin problems and options.autotune is set; the
+// sample is eight problems spread over the batch's sizes, solved for the first
+// three gammas with every candidate (their outputs are overwritten by the run
+// that follows). Other batches and single problems use a cached shape for their
+// key when there is one, else the default.
+static constexpr int kTuneMin = 8;
+
+template <typename Tc>
+static int pick_shape(Ctx* c, const std::vector<HostProblem>& hp, int d, const double* g, int T,
+                      double tol, const ccm_options& o, cudaStream_t s, int* Lout, int* CHout) {
+  const int L0 = default_lanes(d);
+  double sn = 0, sm = 0;
+  for (auto& p : hp) {
+    sn += (double)p.n;
+    sm += (double)p.m;
+  }
+  const double deg = sn > 0 ? 2.0 * sm / sn : 0.0;
+  int bucket = 0;
+  while ((double)(2 << bucket) <= deg && bucket < 30) ++bucket;
+  for (auto& e : c->block_tune)
+    if (e.d == d && e.tc == (int)sizeof(Tc) && e.bucket == bucket) {
+      *Lout = e.L;
+      *CHout = e.CH;
+      return CCM_OK;
+    }
+  *Lout = L0;
+  *CHout = 1;
+  if (!o.autotune || (int)hp.size() < kTuneMin || L0 < 2) return CCM_OK;
+  // sample: eight problems spread over the batch ordered by size
+  std::vector<int> order(hp.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return hp[a].m * 4 + hp[a].n > hp[b].m * 4 + hp[b].n;
+  });
+  std::vector<HostProblem> sample;
+  for (int k = 0; k < kTuneMin; ++k) sample.push_back(hp[order[(size_t)k * hp.size() / kTuneMin]]);
+  const int Ts = std::min(T, 3);
+  std::vector<ccm_stats> st((size_t)sample.size() * Ts);
+  if (c->ev_pool.size() < 2) {
+    while (c->ev_pool.size() < 2) {
+      cudaEvent_t e;
+      CCM_CUDA(cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
+  }
+  float best = 0.f;
+  for (int f = 1; f <= 4 && L0 / f >= 1; f *= 2) {
+    const int L = L0 / f, CH = f;
+    CCM_CUDA(cudaEventRecord(c->ev_pool[0], s));
+    const int r = run_shape<Tc>(c, L, CH, sample, d, g, Ts, tol, o, st.data(), s);
+    if (r != CCM_OK && r != CCM_ERR_NOT_CONVERGED) return r;
+    CCM_CUDA(cudaEventRecord(c->ev_pool[1], s));
+    CCM_CUDA(cudaEventSynchronize(c->ev_pool[1]));
+    float ms = 0.f;
+    CCM_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[0], c->ev_pool[1]));
+    if (f == 1 || ms < best) {
+      best = ms;
+      *Lout = L;
+      *CHout = CH;
+    }
+  }
+  c->block_tune.push_back(BlockTune{d, (int)sizeof(Tc), bucket, *Lout, *CHout});
+  return CCM_OK;
+}
+
 template <typename Tc>
 static int dispatch_block(Ctx* c, const std::vector<HostProblem>& hp, int d, const double* g,
                           int T, double tol, const ccm_options& o, ccm_stats* st,
                           cudaStream_t s) {
-  const int nq = (int)(round_up(d, 4) / 4);
-  if (nq <= 1) return run_block_engine<1, 1, Tc>(c, hp, d, g, T, tol, o, st, s);
-  if (nq <= 2) return run_block_engine<2, 1, Tc>(c, hp, d, g, T, tol, o, st, s);
-  if (nq <= 4) return run_block_engine<4, 1, Tc>(c, hp, d, g, T, tol, o, st, s);
-  if (nq <= 8) return run_block_engine<8, 1, Tc>(c, hp, d, g, T, tol, o, st, s);
-  if (nq <= 16) return run_block_engine<16, 1, Tc>(c, hp, d, g, T, tol, o, st, s);
-  if (nq <= 32) return run_block_engine<32, 1, Tc>(c, hp, d, g, T, tol, o, st, s);
-  set_error("block engine: d = %d above its maximum 128", d);
-  return CCM_ERR_UNSUPPORTED;
+  if (d > 128) {
+    set_error("block engine: d = %d above its maximum 128", d);
+    return CCM_ERR_UNSUPPORTED;
+  }
+  int L = 0, CH = 0;
+  CCM_TRY(pick_shape<Tc>(c, hp, d, g, T, tol, o, s, &L, &CH));
+  c->last_profile.block_lanes = L;
+  c->last_profile.block_quads = CH;
+  return run_shape<Tc>(c, L, CH, hp, d, g, T, tol, o, st, s);
 }
 
 int solve_block(Ctx* c, const std::vector<HostProblem>& hp, int d, const double* gammas, int T,

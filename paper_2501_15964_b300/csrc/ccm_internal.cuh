@@ -48,6 +48,11 @@ enum Slot : int {
   S_XF0, S_XF1, S_KNN, S_REORD, S_COUNT
 };
 
+// Autotuned group shape of the block engine for one (d, precision, degree bucket).
+struct BlockTune {
+  int d, tc, bucket, L, CH;
+};
+
 struct Ctx {
   int device = 0;
   int num_sms = 148;
@@ -64,6 +69,7 @@ struct Ctx {
   // host address as seen by the launching translation unit (each .cu file holds
   // its own instance of a template kernel, so one kernel name can have several)
   std::vector<std::pair<const void*, size_t>> smem_attr;
+  std::vector<BlockTune> block_tune;  // block-engine shapes measured on this context
   // blocks resident on the whole GPU per kernel (occupancy x SMs), keyed like smem_attr
   std::vector<std::pair<const void*, int>> resident;
 };

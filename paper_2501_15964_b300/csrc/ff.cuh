@@ -112,6 +112,38 @@ __device__ __forceinline__ double f32_to_f64_bits(float x) {
                   : __hiloint2double((int)(b & 0x80000000u), 0);
 }
 
+// a <= b for normalised float-float values
+__device__ __forceinline__ bool ff_le(ff a, ff b) { return a.h < b.h || (a.h == b.h && a.l <= b.l); }
+
+// Exact scaling by 1/2.
+__device__ __forceinline__ ff ff_half(ff a) { return ff{0.5f * a.h, 0.5f * a.l}; }
+
+// 1/sqrt(s) for s > 0 (normalised) in float-float: a float32 hardware estimate x0
+// refined by one Newton step for f(x) = 1/x^2 - s,
+//   x1 = x0 + (x0/2)(1 - s x0^2),
+// with x0^2 formed exactly (two-product) and s x0^2 in float-float, so 1 - s x0^2
+// (about 2^-21) is exact to about 2^-46 and x1 carries a relative error of
+// about (3/2) e0^2 + 2^-45, near 2e-13. No float64 operation is used. Outside
+// [1e-30, 1e30], where the float32 estimate loses precision, it goes through
+// float64 (rare).
+__device__ __forceinline__ double ff2d(ff a);
+__device__ __forceinline__ ff ff_rsqrt(ff s) {
+  if (!(s.h > 1e-30f && s.h < 1e30f)) {
+    const double sd = ff2d(s);
+    const double r = 1.0 / sqrt(sd);
+    const float rh = (float)r;
+    return ff{rh, (float)(r - (double)rh)};
+  }
+  const float x0 = rsqrtf(s.h);
+  const float p = x0 * x0;
+  const float pe = fmaf(x0, x0, -p);  // x0^2 = p + pe exactly
+  const ff sx2 = ff_mul(s, ff{p, pe});
+  const float e = (1.0f - sx2.h) - sx2.l;
+  ff r;
+  fast_two_sum(x0, 0.5f * x0 * e, r.h, r.l);
+  return r;
+}
+
 // float-float -> float64: both words converted exactly, one float64 addition.
 __device__ __forceinline__ double ff2d(ff a) { return f32_to_f64_bits(a.h) + f32_to_f64_bits(a.l); }
 

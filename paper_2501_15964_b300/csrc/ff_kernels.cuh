@@ -49,45 +49,51 @@ k_trial_ff(const double* __restrict__ X, const Tc* __restrict__ Dx, const double
     ctl->dots[0] = tot[0];
 }
 
-// Per-edge outputs shared by both passes: kind, alpha, Pi(y) (float-float row),
-// yhat (operator precision) for outside edges. rs = 1/||y||, ny = ||y||.
+// Per-edge scalars and outputs shared by both passes, all in float32 /
+// float-float (no float64 operation per edge): from ss = ||y||^2 and r = gamma
+// w_l, the kind (inert / inside / outside), alpha, Pi(y) (float-float row), yhat
+// (operator precision) for outside edges, and h_l added to hacc.
 template <int LANES, int CH, typename Tc>
-__device__ __forceinline__ uint8_t ff_edge_outputs(const ff (&y)[CH][4], double r, double rs,
-                                                   double ny, int lane, int ld, int64_t e,
-                                                   float2* __restrict__ Ut, Tc* __restrict__ Yh,
-                                                   Tc* __restrict__ alpha,
-                                                   uint8_t* __restrict__ kind) {
+__device__ __forceinline__ uint8_t ff_edge_outputs(const ff (&y)[CH][4], ff r, ff ss, int lane,
+                                                   int ld, int64_t e, float2* __restrict__ Ut,
+                                                   Tc* __restrict__ Yh, Tc* __restrict__ alpha,
+                                                   uint8_t* __restrict__ kind, ff& hacc) {
+  const ff rs = ss.h > 0.0f ? ff_rsqrt(ss) : ff{0.0f, 0.0f};  // 1/||y|| (0 for y = 0)
+  const ff ny = ff_mul(ss, rs);                                // ||y||
   uint8_t kd;
-  double scale;
-  if (!(r > 0.0)) {
-    kd = K_INERT; scale = 0.0;
-  } else if (ny <= r) {
-    kd = K_IN; scale = 1.0;
+  ff scale;
+  if (!(r.h > 0.0f)) {
+    kd = K_INERT;
+    scale = ff{0.0f, 0.0f};
+  } else if (ff_le(ny, r)) {
+    kd = K_IN;
+    scale = ff{1.0f, 0.0f};
   } else {
-    kd = K_OUT; scale = r * rs;
+    kd = K_OUT;
+    scale = ff_mul(r, rs);
   }
   if (lane == 0) {
     kind[e] = kd;
-    alpha[e] = to_operator<Tc>(kd == K_INERT ? 0.0 : scale);
+    alpha[e] = (Tc)scale.h;
+    // h = ||y||^2 / 2 inside the ball, r (||y|| - r/2) outside (0 when r = 0)
+    hacc = ff_add(hacc, ff_le(ny, r) ? ff_half(ss) : ff_mul(r, ff_sub(ny, ff_half(r))));
   }
   if (kd == K_IN) {
     ff_row_store<LANES, CH>(Ut + e * ld, ld, lane, y);  // Pi(y) = y inside the ball
   } else {
-    const ff sc = d2ff(scale);
     ff p[CH][4];
 #pragma unroll
     for (int c = 0; c < CH; ++c)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) p[c][k] = kd == K_INERT ? ff{0.0f, 0.0f} : ff_mul(y[c][k], sc);
+      for (int k = 0; k < 4; ++k) p[c][k] = kd == K_INERT ? ff{0.0f, 0.0f} : ff_mul(y[c][k], scale);
     ff_row_store<LANES, CH>(Ut + e * ld, ld, lane, p);
   }
   if (kd == K_OUT) {
-    const float inv = (float)f64_to_f32_rz(rs);
     Tc yh[CH][4];
 #pragma unroll
     for (int c = 0; c < CH; ++c)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)(y[c][k].h * inv);
+      for (int k = 0; k < 4; ++k) yh[c][k] = (Tc)(y[c][k].h * rs.h);
     row_store<LANES, CH>(Yh + e * ld, ld, lane, yh);
   }
   return kd;
@@ -105,11 +111,12 @@ k_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
   const unsigned mask = group_mask<LANES>();
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
-  const ff sg = d2ff(sigma);
-  double acc[2] = {0.0, 0.0};
+  const ff sg = d2ff(sigma), gm = d2ff(gamma);
+  ff hacc = {0.0f, 0.0f};
+  int nout = 0;
   for (int64_t e = g0; e < m; e += ng) {
     const int2 ij = edges[e];
-    const double r = gamma * w[e];
+    const ff r = ff_mul(gm, d2ff(w[e]));
     ff xi[CH][4], xj[CH][4], y[CH][4];
     ff_row_load<LANES, CH>(XF + (int64_t)ij.x * ld, ld, lane, xi);
     ff_row_load<LANES, CH>(XF + (int64_t)ij.y * ld, ld, lane, xj);
@@ -122,16 +129,12 @@ k_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
         y[c][k] = ff_add(y[c][k], ff_mul(ff_sub(xi[c][k], xj[c][k]), sg));
         ff_sqr_acc(ss, y[c][k]);
       }
-    const double s2 = ff2d(ff_group_sum<LANES>(ff_norm(ss), mask));
-    const double rs = s2 > 0.0 ? rsqrt_refined(s2) : 0.0;
-    const double ny = s2 * rs;
-    const uint8_t kd = ff_edge_outputs<LANES, CH, Tc>(y, r, rs, ny, lane, ld, e, Ut, Yh, alpha,
-                                                      kind);
-    if (lane == 0) {
-      acc[0] += (ny <= r) ? 0.5 * s2 : r * ny - 0.5 * r * r;
-      acc[1] += (kd == K_OUT) ? 1.0 : 0.0;
-    }
+    ss = ff_group_sum<LANES>(ff_norm(ss), mask);
+    const uint8_t kd =
+        ff_edge_outputs<LANES, CH, Tc>(y, r, ss, lane, ld, e, Ut, Yh, alpha, kind, hacc);
+    if (lane == 0) nout += kd == K_OUT ? 1 : 0;
   }
+  double acc[2] = {ff2d(hacc), (double)nout};
   double tot[2];
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_EVAL_E], tot) && threadIdx.x == 0) {
     ctl->eval[0] = tot[0];
@@ -154,11 +157,12 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
   const unsigned mask = group_mask<LANES>();
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
-  const ff sg = d2ff(sigma);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // ||res||^2, sum r||bx||, sum h, #outside
+  const ff sg = d2ff(sigma), gm = d2ff(gamma);
+  ff racc = {0.0f, 0.0f}, pacc = {0.0f, 0.0f}, hacc = {0.0f, 0.0f};  // ||res||^2, sum r||bx||, sum h
+  int nout = 0;
   for (int64_t e = g0; e < m; e += ng) {
     const int2 ij = edges[e];
-    const double r = gamma * w[e];
+    const ff r = ff_mul(gm, d2ff(w[e]));
     ff bx[CH][4], v[CH][4], y[CH][4];
     ff_row_load<LANES, CH>(XF + (int64_t)ij.x * ld, ld, lane, bx);
     ff_row_load<LANES, CH>(XF + (int64_t)ij.y * ld, ld, lane, y);
@@ -176,14 +180,15 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
         ff_sqr_acc(ss, y[c][k]);
         ff_sqr_acc(sv, v[c][k]);
       }
-    const double b2 = ff2d(ff_group_sum<LANES>(ff_norm(sb), mask));
-    const double v2 = ff2d(ff_group_sum<LANES>(ff_norm(sv), mask));
-    const double s2 = ff2d(ff_group_sum<LANES>(ff_norm(ss), mask));
-    const double rv = v2 > 0.0 ? rsqrt_refined(v2) : 0.0;
-    const double shrink = (v2 * rv > r) ? 1.0 - r * rv : 0.0;
+    sb = ff_group_sum<LANES>(ff_norm(sb), mask);
+    sv = ff_group_sum<LANES>(ff_norm(sv), mask);
+    ss = ff_group_sum<LANES>(ff_norm(ss), mask);
+    // shrink = 1 - r / ||v|| where ||v|| > r, else 0
+    const ff rv = sv.h > 0.0f ? ff_rsqrt(sv) : ff{0.0f, 0.0f};
+    const ff nsh = ff_le(ff_mul(sv, rv), r) ? ff{0.0f, 0.0f}
+                                            : ff_sub(ff_mul(r, rv), ff{1.0f, 0.0f});  // -shrink
     // residual bx - shrink v: its norm only enters eta_P, so its square is summed
     // in float32 from the float-float difference
-    const ff nsh = d2ff(-shrink);
     float sres = 0.0f;
 #pragma unroll
     for (int c = 0; c < CH; ++c)
@@ -192,17 +197,16 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
         const ff res = ff_add(bx[c][k], ff_mul(v[c][k], nsh));
         sres = fmaf(res.h, res.h, sres);
       }
-    acc[0] += (double)sres;
-    const double rs = s2 > 0.0 ? rsqrt_refined(s2) : 0.0;
-    const double ny = s2 * rs;
-    const uint8_t kd = ff_edge_outputs<LANES, CH, Tc>(y, r, rs, ny, lane, ld, e, Ut, Yh, alpha,
-                                                      kind);
+    racc = ff_add(racc, ff{sres, 0.0f});
+    const uint8_t kd =
+        ff_edge_outputs<LANES, CH, Tc>(y, r, ss, lane, ld, e, Ut, Yh, alpha, kind, hacc);
     if (lane == 0) {
-      acc[1] += b2 > 0.0 ? r * (b2 * rsqrt_refined(b2)) : 0.0;
-      acc[2] += (ny <= r) ? 0.5 * s2 : r * ny - 0.5 * r * r;
-      acc[3] += (kd == K_OUT) ? 1.0 : 0.0;
+      if (sb.h > 0.0f) pacc = ff_add(pacc, ff_mul(r, ff_mul(sb, ff_rsqrt(sb))));
+      nout += kd == K_OUT ? 1 : 0;
     }
   }
+  // the residual sums of all lanes join; the per-edge terms were added by lane 0 only
+  double acc[4] = {ff2d(racc), ff2d(pacc), ff2d(hacc), (double)nout};
   double tot[4];
   if (grid_reduce<4>(acc, partials, &ctl->counter[C_KKT_E], tot) && threadIdx.x == 0) {
     ctl->kkt[0] = tot[0];

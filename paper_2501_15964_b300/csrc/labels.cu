@@ -41,8 +41,10 @@ __global__ void k_lab_hook(const double* __restrict__ X, int64_t ldx, int d,
     int2 ij = edges[e];
     const double* xi = X + (int64_t)ij.x * ldx;
     const double* xj = X + (int64_t)ij.y * ldx;
+    // the partial sums of non-negative terms never decrease, so the sum stops as
+    // soon as it passes the threshold: the decision is the one of the full sum
     double acc = 0.0;
-    for (int k = 0; k < d; ++k) {
+    for (int k = 0; k < d && acc <= 1e-12; ++k) {
       double dl = __dsub_rn(xi[k], xj[k]);
       acc = __dadd_rn(acc, __dmul_rn(dl, dl));
     }

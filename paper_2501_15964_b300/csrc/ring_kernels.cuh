@@ -143,8 +143,9 @@ k_cg_matvec_ring(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc
         const int src = (int)(pk - c_base);
         const int ex = __shfl_sync(0xffffffffu, c_eo.x, src);
         const int ey = __shfl_sync(0xffffffffu, c_eo.y, src);
-        const Tc mc = __shfl_sync(0xffffffffu, c_m.c, src);
+        const Tc mc_raw = __shfl_sync(0xffffffffu, c_m.c, src);
         const Tc mo = __shfl_sync(0xffffffffu, c_m.mo, src);
+        const Tc mc = inc_ok(make_int2(ex, ey), B_MATVEC_RING, pk) ? mc_raw : (Tc)0;
         smeta[pslot].c = mc;  // every lane writes the same value and reads it back itself
         smeta[pslot].mo = mo;
         if (mc != (Tc)0) {

@@ -8,6 +8,7 @@
 // one host read-back per chunk.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "ccm_internal.cuh"
 #include "solve_common.cuh"
@@ -373,6 +374,19 @@ struct GridEngine {
     CCM_TRY(build_csr(c, edges, m, n, &off, &inc, s));
     // long rows: the shared-memory ring kernels over an even split of the
     // incidence stream (one span per warp)
+#ifdef CCM_DEBUG_BOUNDS
+    {
+      const DebugBounds hb{(long long)n, (long long)m, 0, 0, 0};
+      CCM_CUDA(cudaMemcpyToSymbolAsync(g_bounds, &hb, sizeof(hb), 0, cudaMemcpyHostToDevice, s));
+      // fault injection for the tests of this build: one incidence record gets an
+      // out-of-range endpoint, which the checks must catch before any access
+      if (getenv("CCM_DEBUG_CORRUPT") && m > 0) {
+        const int bad = (int)n + 3;
+        CCM_CUDA(cudaMemcpyAsync(&inc[0].y, &bad, sizeof(int), cudaMemcpyHostToDevice, s));
+        CCM_CUDA(cudaStreamSynchronize(s));
+      }
+    }
+#endif
     RingPlan rp;
     CCM_TRY(ring_plan<Tc>(c, L, ld, off, n, rp, s));
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
@@ -406,6 +420,18 @@ struct GridEngine {
     auto readback = [&]() -> int {
       CCM_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
       CCM_CUDA(cudaStreamSynchronize(s));
+#ifdef CCM_DEBUG_BOUNDS
+      DebugBounds hb{};
+      CCM_CUDA(cudaMemcpyFromSymbol(&hb, g_bounds, sizeof(hb)));
+      if (hb.err) {
+        static const char* names[] = {"?", "k_cg_init", "k_cg_matvec", "k_cg_matvec_ring"};
+        set_error("index check failed in %s at incidence record %lld (bounds-checked build)",
+                  names[(hb.where >= 1 && hb.where <= 3) ? hb.where : 0], hb.index);
+        const DebugBounds z{0, 0, 0, 0, 0};
+        CCM_CUDA(cudaMemcpyToSymbol(g_bounds, &z, sizeof(z)));
+        return CCM_ERR_BOUNDS;
+      }
+#endif
       return CCM_OK;
     };
     CCM_TRY(readback());

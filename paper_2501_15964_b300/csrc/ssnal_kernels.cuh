@@ -32,6 +32,35 @@ enum EdgeKind : uint8_t { K_INERT = 0, K_IN = 1, K_OUT = 2, K_MASK = 3, K_LINF =
 // The int32 value of q that selects q = inf.
 constexpr int kQInf = CCM_Q_INF;
 
+// Bounds-checked build (CCM_DEBUG_BOUNDS): the kernels that gather through the
+// CSR incidence records check each record's edge id and other endpoint against
+// the problem's sizes before touching memory; a bad record is skipped and the
+// first one is recorded here (no trap), and the host turns it into
+// CCM_ERR_BOUNDS. One copy per translation unit; the grid engine's host code
+// sets the sizes before its launches (a unit that never sets them, n = 0, is
+// not checked).
+struct DebugBounds {
+  long long n, m;
+  int err, where;
+  long long index;
+};
+#ifdef CCM_DEBUG_BOUNDS
+static __device__ DebugBounds g_bounds;
+__device__ __forceinline__ bool inc_ok(int2 eo, int where, long long idx) {
+  if (g_bounds.n == 0) return true;
+  const bool ok = eo.x >= 0 && eo.x < g_bounds.m && eo.y >= 0 && eo.y < g_bounds.n;
+  if (!ok && atomicCAS(&g_bounds.err, 0, 1) == 0) {
+    g_bounds.where = where;
+    g_bounds.index = idx;
+  }
+  return ok;
+}
+#else
+__device__ __forceinline__ bool inc_ok(int2, int, long long) { return true; }
+#endif
+// Kernels named by DebugBounds::where.
+enum BoundsSite { B_CG_INIT = 1, B_MATVEC = 2, B_MATVEC_RING = 3 };
+
 // Device-resident scalars of one solve (one problem).
 struct CgCtl {
   double rz, rr, tol2, alpha, beta;
@@ -193,7 +222,19 @@ k_edge_eval(const double* __restrict__ X, const double* __restrict__ U,
 // added one by one in increasing edge id (the same order for every run).
 template <int CH>
 struct GatherDepth {
-  static constexpr int v = CH == 1 ? 4 : (CH == 2 ? 2 : 1);
+  static constexpr int v = CH <= 2 ? 4 : 1;
+};
+
+// Group shape of the register-form operator for an operator shape (LANES, CH):
+// rows of one quad per lane on 8 or more lanes run on half as many lanes with
+// two quads each, which halves the per-incidence overhead (record broadcasts,
+// loop control) and the levels of the per-edge group sums (measured: 0.58 ->
+// 0.54 ms per launch at n = 200,000, d = 50; the node gradient, whose work is
+// per element, was slower in that shape and keeps one quad per lane).
+template <int LANES, int CH>
+struct GatherShape {
+  static constexpr int L = (CH == 1 && LANES >= 8) ? LANES / 2 : LANES;
+  static constexpr int C = CH * LANES / L;
 };
 
 template <typename Tc>
@@ -323,6 +364,10 @@ k_cg_init(const double* __restrict__ G, const Tc* __restrict__ Minv, Tc* __restr
   if (meta)
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ninc; t += stride) {
       const int2 eo = inc[t];
+      if (!inc_ok(eo, B_CG_INIT, t)) {
+        meta[t] = IncMeta<Tc>{(Tc)0, (Tc)0};  // the record is skipped
+        continue;
+      }
       const uint8_t kd = kind[eo.x];
       IncMeta<Tc> mm;
       mm.c = kd == K_IN ? (Tc)1
@@ -475,7 +520,7 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
           const int ey = __shfl_sync(mask, rec.y, j + kk, LANES);
           cs[kk] = __shfl_sync(mask, mm.c, j + kk, LANES);
           mos[kk] = __shfl_sync(mask, mm.mo, j + kk, LANES);
-          if (j + kk >= nb) cs[kk] = (Tc)0;
+          if (j + kk >= nb || !inc_ok(make_int2(ex, ey), B_MATVEC, base + j + kk)) cs[kk] = (Tc)0;
           if (cs[kk] != (Tc)0) {
             row_load<LANES, CH>(R + (int64_t)ey * ld, ld, lane, v0[kk]);
           } else {
@@ -999,8 +1044,9 @@ inline int launch_matvec_reg(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, 
                              const int2* inc, double sigma, int64_t n, int ld, double* part,
                              Ctl* ctl, cudaStream_t s) {
   const int threads = 256;
-  const int gpb = threads / L;
-  auto fn = k_cg_matvec<L, CH, Tc>;
+  using GS = GatherShape<L, CH>;
+  const int gpb = threads / GS::L;
+  auto fn = k_cg_matvec<GS::L, GS::C, Tc>;
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)resident_grid(c, fn, threads)));
   fn<<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma, n, ld, part, ctl);

@@ -80,3 +80,17 @@ def test_binding_constants_match_header():
     o = Options()
     ccm.load_library().ccm_default_options(C.byref(o))
     assert o.sigma_max <= 0.0 and o.sigma0 == 1.0
+
+
+def test_bounds_checked_library_exports_every_declared_symbol(lib):
+    """The CCM_DEBUG_BOUNDS build (libccm_debug.so) is the same ABI."""
+    from paper_2501_15964_b300 import build as b
+    from paper_2501_15964_b300._lib import debug_lib_path
+    path = debug_lib_path()
+    if not os.path.exists(path):
+        b.build(debug=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (ccm_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing

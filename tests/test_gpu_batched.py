@@ -129,3 +129,24 @@ def test_batched_config_sized_problems(ccm):
             assert np.linalg.norm(xb - xg) <= TOL * np.linalg.norm(xg), t
             lab = olabels.labels(xb, E)
             assert np.array_equal(Lb[t].cpu().numpy(), lab)
+
+
+def test_batched_autotuned_shape_matches_default(ccm):
+    """A batch of >= 8 problems measures the candidate group shapes (lanes x
+    quads per row) on a sample and keeps the fastest; whichever it picks, the
+    solutions agree with the default shape's within 1e-6 and every gamma meets
+    the tolerance."""
+    probs = _problems(12, 23, 60, 200, d=16)
+    dev = [_dev(*p) for p in probs]
+    g = synth.gamma_grid(1e-3, 1e2, 6)
+    Xt, Lt, st = ccm.solve_path_batched(dev, g, tol=SOLVE_TOL, autotune=1)
+    prof = ccm.last_profile()
+    assert (prof["block_lanes"], prof["block_quads"]) in [(4, 1), (2, 2), (1, 4)], prof
+    ctx2 = ccm.Context(0)
+    X0, L0, st0 = ccm.solve_path_batched(dev, g, tol=SOLVE_TOL, autotune=0, ctx=ctx2)
+    assert ccm.last_profile(ctx2)["block_lanes"] == 4
+    for a, b, s1 in zip(Xt, X0, st):
+        assert all(s["status"] == 0 and s["kkt"] <= TOL and s["gap"] <= TOL for s in s1)
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        for t in range(len(g)):
+            assert np.linalg.norm(a[t] - b[t]) <= TOL * np.linalg.norm(b[t])
