@@ -40,6 +40,29 @@ SOLVE_TOL = 2e-7    # solver stop: tighter, so X is within 1e-6 of the oracle
 METRIC = "gamma-solves/s at KKT<=1e-6 (graph build + path solve)"
 
 
+def operator_kernel(d, precision="mixed"):
+    """Name of the Newton-CG operator kernel the grid engine launches for rows of
+    d features (the same dispatch as the library: rows of up to 16 quads use the
+    register form, halved to two quads per lane from 8 lanes; longer rows the
+    shared-memory ring form)."""
+    tc = "float" if precision == "mixed" else "double"
+    nq = -(-d // 4)
+    if nq <= 16:
+        lanes = 1
+        while lanes < nq:
+            lanes *= 2
+        lanes, quads = (lanes // 2, 2) if lanes >= 8 else (lanes, 1)
+        return f"k_cg_matvec<{lanes}, {quads}, {tc}>"
+    return f"k_cg_matvec_ring<{-(-nq // 32)}, {tc}, 4>"
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one operator
+# launch from an ncu capture of the current kernel on the workload, per launch;
+# every launch of the n = 200,000, phi = 0.5 path has every edge outside the
+# ball, so one launch stands for all of them (profiles/k_cg_matvec_gmm200k_d50.md).
+OPERATOR_TRAFFIC = {("gmm200k_d50", "mixed"): 687450112 + 40448768}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -473,14 +496,16 @@ def main():
                        "edges": int(E.shape[0]),
                        "l2": "inputs larger than L2 (per-step working set > 1 GB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "kernel": "k_cg_matvec",
+            "roofline": {"bound": "hbm", "kernel": operator_kernel(A.shape[1], args.precision),
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
                          "nominal_peak": NOMINAL_HBM_GBS,
                          "launches_timed": int(mv_n),
-                         "ms_per_step": mv_ms / args.steps, "traffic": None},
+                         "ms_per_step": mv_ms / args.steps,
+                         "traffic": OPERATOR_TRAFFIC.get((WORKLOAD, args.precision)),
+                         "algorithmic_bytes_per_launch": (mv_bytes / mv_n) if mv_n else None},
             "e2e": {"value": e2e, "unit": "gamma-solves/s",
                     "h2d_bytes_per_step": int(A.nbytes),
                     "d2h_bytes_per_step": int(X_host.numel() * 8 + L_host.numel() * 4)},
