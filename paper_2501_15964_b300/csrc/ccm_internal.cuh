@@ -45,7 +45,7 @@ enum Slot : int {
   S_U, S_UT, S_YH, S_ALPHA, S_KIND, S_EDGES, S_CSR_OFF, S_CSR_INC, S_PART, S_CTRL,
   S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
   S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3, S_META, S_WPART, S_VJPF, S_ADMM,
-  S_XF0, S_XF1, S_KNN, S_REORD, S_COUNT
+  S_XF0, S_XF1, S_KNN, S_REORD, S_ORDER, S_ORDER_TMP, S_COUNT
 };
 
 // Autotuned group shape of the block engine for one (d, precision, degree bucket).
@@ -286,6 +286,9 @@ struct Relabel {
 };
 int locality_relabel(Ctx* c, const int2* edges, const double* w, int64_t m, int64_t n,
                      Relabel& r, cudaStream_t s);
+// Visiting order of the register-form gathers (reorder.cu): windows of 4,096 nodes
+// in index order, by decreasing degree inside a window. ord: device n int32.
+int degree_order(Ctx* c, const int64_t* off, int64_t n, int* ord, cudaStream_t s);
 
 // Scan helpers (device-wide exclusive scan of int32 / int64).
 int scan_exclusive_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_host,

@@ -224,7 +224,8 @@ k_node_grad_ff(const double* __restrict__ X, const double* __restrict__ Ap,
                const float2* __restrict__ Ut, const int64_t* __restrict__ off,
                const int2* __restrict__ inc, const Tc* __restrict__ alpha,
                const uint8_t* __restrict__ kind, double sigma, int d, double* __restrict__ G,
-               Tc* __restrict__ Minv, int64_t n, int ld, double* partials, Ctl* ctl) {
+               Tc* __restrict__ Minv, int64_t n, int ld, double* partials, Ctl* ctl,
+               const int* __restrict__ ord) {
   constexpr int NB = GatherDepth<CH>::v;
   const int lane = threadIdx.x % LANES;
   const unsigned mask = group_mask<LANES>();
@@ -232,7 +233,8 @@ k_node_grad_ff(const double* __restrict__ X, const double* __restrict__ Ap,
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
   const float tr_out = (float)(d - 1) / (float)d;
   double acc[2] = {0.0, 0.0};
-  for (int64_t i = g0; i < n; i += ng) {
+  for (int64_t gi = g0; gi < n; gi += ng) {
+    const int64_t i = ord ? (int64_t)ord[gi] : gi;  // visiting order (see degree_order)
     const int64_t b = off[i], eend = off[i + 1];
     ff g[CH][4];
 #pragma unroll
@@ -492,7 +494,7 @@ inline int launch_node_grad_ff(Ctx* c, const double* X, const double* Ap, const 
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)resident_grid(c, fn, threads)));
     fn<<<blocks, threads, 0, s>>>(X, Ap, Ut, off, inc, alpha, kind, sigma, d, G, Minv, n, ld,
-                                  part, ctl);
+                                  part, ctl, rp.ord);
   }
   CCM_COUNT(c);
   return CCM_OK;

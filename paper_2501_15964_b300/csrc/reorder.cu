@@ -176,6 +176,50 @@ __global__ void k_edge_emit(const unsigned long long* __restrict__ key,
   }
 }
 
+// ---------------------------------------------------------------- processing order
+// Order in which the register-form gathers visit nodes: windows of 2^wshift
+// consecutive nodes in index order, inside a window by decreasing degree (stable).
+// The groups of a warp then own nodes of (nearly) equal degree and run their
+// incidence loops for the same number of iterations, while the window keeps the
+// sweep local in the node order.
+__global__ void k_degree_keys(const int64_t* __restrict__ off, int64_t n, int wshift,
+                              unsigned long long* __restrict__ key, int* __restrict__ val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t deg = off[i + 1] - off[i];
+    const unsigned long long inv = 65535ull - (unsigned long long)(deg < 65535 ? deg : 65535);
+    key[i] = ((unsigned long long)(i >> wshift) << 16) | inv;
+    val[i] = (int)i;
+  }
+}
+
+int degree_order(Ctx* c, const int64_t* off, int64_t n, int* ord, cudaStream_t s) {
+  const int wshift = 12;
+  const int threads = 256;
+  const int blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8));
+  const int64_t nblk = (n + 255) / 256;
+  const size_t b_k = round_up(n * 8, 256), b_v = round_up(n * 4, 256),
+               b_c = round_up(256 * nblk * 8, 256);
+  void* p;
+  CCM_TRY(ws_get(c, S_ORDER_TMP, 2 * b_k + 2 * b_v + 2 * b_c, &p));
+  char* q = (char*)p;
+  unsigned long long* k0 = (unsigned long long*)q;
+  unsigned long long* k1 = (unsigned long long*)(q + b_k);
+  int* v0 = (int*)(q + 2 * b_k);
+  int* v1 = (int*)(q + 2 * b_k + b_v);
+  int64_t* cnt = (int64_t*)(q + 2 * b_k + 2 * b_v);
+  int64_t* offs = (int64_t*)(q + 2 * b_k + 2 * b_v + b_c);
+  k_degree_keys<<<blocks, threads, 0, s>>>(off, n, wshift, k0, v0);
+  CCM_COUNT(c);
+  unsigned long long* kr;
+  int* vr;
+  const int bits = bit_width((((uint64_t)(n - 1)) >> wshift << 16) | 65535ull);
+  CCM_TRY(radix_sort(c, k0, v0, k1, v1, n, bits, cnt, offs, &kr, &vr, s));
+  CCM_CUDA(cudaMemcpyAsync(ord, vr, n * 4, cudaMemcpyDeviceToDevice, s));
+  return CCM_OK;
+}
+
 int locality_relabel(Ctx* c, const int2* edges, const double* w, int64_t m, int64_t n,
                      Relabel& r, cudaStream_t s) {
   const int threads = 256;

@@ -495,6 +495,7 @@ struct RingPlan {
   void* parts = nullptr;      // 2 nwg rows of ld float64 (operator parts use the first half as Tc)
   double* pdiag = nullptr;    // 2 nwg
   unsigned* cnt = nullptr;    // nwg counters (zero between launches)
+  const int* ord = nullptr;   // register forms: node visiting order (null: index order)
   bool on() const { return spans != nullptr; }
 };
 
@@ -556,7 +557,7 @@ inline int launch_matvec(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, Tc* 
     return CCM_OK;
   }
   return launch_matvec_reg<L, CH, Tc>(c, R, Minv, Dg, W, Yh, meta, off, inc, sigma, n, ld, part,
-                                      ctl, s);
+                                      ctl, s, rp.ord);
 }
 
 // Node gradient: the ring form when a plan is given, the register form otherwise.

@@ -20,6 +20,8 @@ namespace ccm {
 
 // node count from which ccm_solve_path relabels nodes by graph component
 static constexpr int64_t kRelabelMinN = 16384;
+// node count from which the register-form gathers visit nodes in degree order
+static constexpr int64_t kDegreeOrderMinN = 8192;
 
 // Row gather into the padded layout / scatter back out of it. idx (optional)
 // maps a padded row to its source / destination row; a complemented entry (~r)
@@ -389,6 +391,13 @@ struct GridEngine {
 #endif
     RingPlan rp;
     CCM_TRY(ring_plan<Tc>(c, L, ld, off, n, rp, s));
+    // register forms with several row groups per warp: visit nodes of equal degree
+    // together (windows of 4,096 nodes by decreasing degree)
+    if (!rp.on() && L < 32 && n >= kDegreeOrderMinN) {
+      CCM_TRY(get(S_ORDER, n * 4, &p));
+      CCM_TRY(degree_order(c, off, n, (int*)p, s));
+      rp.ord = (const int*)p;
+    }
     CCM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     k_gather_rows<<<b_elem, threads, 0, s>>>(a.A, Ap, n, d, ld, a.perm);
     CCM_COUNT(c);

@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(256)
 k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __restrict__ Dg,
             Tc* __restrict__ W, const Tc* __restrict__ Yh, const IncMeta<Tc>* __restrict__ meta,
             const int64_t* __restrict__ off, const int2* __restrict__ inc, double sigma,
-            int64_t n, int ld, double* partials, Ctl* ctl) {
+            int64_t n, int ld, double* partials, Ctl* ctl, const int* __restrict__ ord) {
   if (!ctl->cg.active) return;
   constexpr int NB = GatherDepth<CH>::v;
   const int lane = threadIdx.x % LANES;
@@ -489,7 +489,8 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
   const Tc sg = (Tc)sigma;
   Tc dot = (Tc)0, dot_e = (Tc)0;  // <W, u> over this thread's elements, float-float
-  for (int64_t i = g0; i < n; i += ng) {
+  for (int64_t gi = g0; gi < n; gi += ng) {
+    const int64_t i = ord ? (int64_t)ord[gi] : gi;  // visiting order (see degree_order)
     Tc u[CH][4], accv[CH][4];
     const Tc mi = Minv[i];
     row_load<LANES, CH>(R + i * ld, ld, lane, u);
@@ -1042,14 +1043,14 @@ template <int L, int CH, typename Tc>
 inline int launch_matvec_reg(Ctx* c, const Tc* R, const Tc* Minv, const Tc* Dg, Tc* W,
                              const Tc* Yh, const IncMeta<Tc>* meta, const int64_t* off,
                              const int2* inc, double sigma, int64_t n, int ld, double* part,
-                             Ctl* ctl, cudaStream_t s) {
+                             Ctl* ctl, cudaStream_t s, const int* ord = nullptr) {
   const int threads = 256;
   using GS = GatherShape<L, CH>;
   const int gpb = threads / GS::L;
   auto fn = k_cg_matvec<GS::L, GS::C, Tc>;
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>((n + gpb - 1) / gpb, (int64_t)resident_grid(c, fn, threads)));
-  fn<<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma, n, ld, part, ctl);
+  fn<<<blocks, threads, 0, s>>>(R, Minv, Dg, W, Yh, meta, off, inc, sigma, n, ld, part, ctl, ord);
   CCM_COUNT(c);
   return CCM_OK;
 }
