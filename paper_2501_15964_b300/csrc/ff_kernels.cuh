@@ -147,7 +147,7 @@ k_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
 // (= ||bx - shrink v||^2 with v = u + bx, shrink = max(0, 1 - r/||v||)) and
 // r_l ||bx|| for f_p, and y = u + sigma bx the evaluation outputs.
 template <int LANES, int CH, typename Tc>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, CH <= 4 ? 2 : 1)
 k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
                    const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
                    double sigma, float2* __restrict__ Ut, Tc* __restrict__ Yh,
@@ -163,22 +163,29 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
   for (int64_t e = g0; e < m; e += ng) {
     const int2 ij = edges[e];
     const ff r = ff_mul(gm, d2ff(w[e]));
-    ff bx[CH][4], v[CH][4], y[CH][4];
-    ff_row_load<LANES, CH>(XF + (int64_t)ij.x * ld, ld, lane, bx);
-    ff_row_load<LANES, CH>(XF + (int64_t)ij.y * ld, ld, lane, y);
-    ff_row_load<LANES, CH>(U + e * ld, ld, lane, v);
+    // u and bx are the edge's rows; v = u + bx and y = u + sigma bx are formed
+    // from them where they are needed (by the same operations each time, so
+    // with the same values), and the launch bounds ask for two resident blocks
+    // per SM where a lane holds at most four quads
+    ff bx[CH][4], u[CH][4];
+    {
+      ff xj[CH][4];
+      ff_row_load<LANES, CH>(XF + (int64_t)ij.x * ld, ld, lane, bx);
+      ff_row_load<LANES, CH>(XF + (int64_t)ij.y * ld, ld, lane, xj);
+      ff_row_load<LANES, CH>(U + e * ld, ld, lane, u);
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bx[c][k] = ff_sub(bx[c][k], xj[c][k]);
+    }
     ff sb = {0.0f, 0.0f}, sv = {0.0f, 0.0f}, ss = {0.0f, 0.0f};
 #pragma unroll
     for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        bx[c][k] = ff_sub(bx[c][k], y[c][k]);
-        const ff u = v[c][k];
-        y[c][k] = ff_add(u, ff_mul(bx[c][k], sg));
-        v[c][k] = ff_add(u, bx[c][k]);
         ff_sqr_acc(sb, bx[c][k]);
-        ff_sqr_acc(ss, y[c][k]);
-        ff_sqr_acc(sv, v[c][k]);
+        ff_sqr_acc(ss, ff_add(u[c][k], ff_mul(bx[c][k], sg)));
+        ff_sqr_acc(sv, ff_add(u[c][k], bx[c][k]));
       }
     sb = ff_group_sum<LANES>(ff_norm(sb), mask);
     sv = ff_group_sum<LANES>(ff_norm(sv), mask);
@@ -194,12 +201,17 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
     for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const ff res = ff_add(bx[c][k], ff_mul(v[c][k], nsh));
+        const ff res = ff_add(bx[c][k], ff_mul(ff_add(u[c][k], bx[c][k]), nsh));
         sres = fmaf(res.h, res.h, sres);
       }
     racc = ff_add(racc, ff{sres, 0.0f});
+    // y = u + sigma bx in place of u
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) u[c][k] = ff_add(u[c][k], ff_mul(bx[c][k], sg));
     const uint8_t kd =
-        ff_edge_outputs<LANES, CH, Tc>(y, r, ss, lane, ld, e, Ut, Yh, alpha, kind, hacc);
+        ff_edge_outputs<LANES, CH, Tc>(u, r, ss, lane, ld, e, Ut, Yh, alpha, kind, hacc);
     if (lane == 0) {
       if (sb.h > 0.0f) pacc = ff_add(pacc, ff_mul(r, ff_mul(sb, ff_rsqrt(sb))));
       nout += kd == K_OUT ? 1 : 0;
@@ -233,9 +245,24 @@ k_node_grad_ff(const double* __restrict__ X, const double* __restrict__ Ap,
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
   const float tr_out = (float)(d - 1) / (float)d;
   double acc[2] = {0.0, 0.0};
+  // The chain of dependent scalar loads in front of a node's gathers (its index
+  // in the visiting order, then its row range) is pipelined across the group's
+  // nodes: the range of the next node and the index of the one after it are
+  // loaded while this node is processed.
+  auto node_of = [&](int64_t gi) -> int64_t {
+    return gi < n ? (ord ? (int64_t)ord[gi] : gi) : 0;
+  };
+  int64_t i_cur = node_of(g0);
+  int64_t b_cur = g0 < n ? off[i_cur] : 0, e_cur = g0 < n ? off[i_cur + 1] : 0;
+  int64_t i_nxt = node_of(g0 + ng);
   for (int64_t gi = g0; gi < n; gi += ng) {
-    const int64_t i = ord ? (int64_t)ord[gi] : gi;  // visiting order (see degree_order)
-    const int64_t b = off[i], eend = off[i + 1];
+    const int64_t i = i_cur, b = b_cur, eend = e_cur;
+    if (gi + ng < n) {
+      b_cur = off[i_nxt];
+      e_cur = off[i_nxt + 1];
+    }
+    i_cur = i_nxt;
+    i_nxt = node_of(gi + 2 * ng);
     ff g[CH][4];
 #pragma unroll
     for (int c = 0; c < CH; ++c)
@@ -279,6 +306,9 @@ k_node_grad_ff(const double* __restrict__ X, const double* __restrict__ Ap,
               g[c][k] = ff_add(g[c][k], neg[kk] ? ff_neg(u[kk][c][k]) : u[kk][c][k]);
       }
     }
+    // the X and A rows are loaded here, after the gathers: loading them first
+    // (16 more registers at one quad per lane) cost a resident block per SM and
+    // was slower (636 against 481 us on 200,000 nodes of degree 17)
     double gd[CH][4], xa[CH][4], a4[CH][4];
     row_load<LANES, CH>(X + i * ld, ld, lane, xa);
     row_load<LANES, CH>(Ap + i * ld, ld, lane, a4);

@@ -332,6 +332,10 @@ struct GridEngine {
     const int gpb_e = threads / ES::L;
     const int b_edge2 =
         (int)std::max<int64_t>(1, std::min<int64_t>((m + gpb_e - 1) / gpb_e, 2 * maxb));
+    using FS = FfEdgeShape<L, CH>;  // the float-float edge passes
+    const int gpb_f = threads / FS::L;
+    const int b_edge_ff =
+        (int)std::max<int64_t>(1, std::min<int64_t>((m + gpb_f - 1) / gpb_f, 2 * maxb));
     const int b_elem = nb(nl);
     const int b_quad = nb((nl + 3) / 4);
 
@@ -473,7 +477,7 @@ struct GridEngine {
     auto evaluate = [&](const double* Xc, const float2* XFc, double* phi, double* gn,
                         double* nout) -> int {
       if (FF) {
-        k_edge_eval_ff<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
+        k_edge_eval_ff<FS::L, FS::C, Tc><<<b_edge_ff, threads, 0, s>>>(
             XFc, (const float2*)U, edges, a.w, gamma_cur, sigma, (float2*)Ut, Yh, alpha, kind, m,
             ld, part, ctl);
         CCM_COUNT(c);
@@ -611,7 +615,7 @@ struct GridEngine {
           k_kkt_edge_eval_qn<kQInf, L, CH, Tc><<<b_edge, threads, 0, s>>>(
               X, U, edges, a.w, gamma, sigma, Ut, Yh, alpha, kind, m, d, ld, part, ctl);
         else if (FF)
-          k_kkt_edge_eval_ff<ES::L, ES::C, Tc><<<b_edge2, threads, 0, s>>>(
+          k_kkt_edge_eval_ff<FS::L, FS::C, Tc><<<b_edge_ff, threads, 0, s>>>(
               XF, (const float2*)U, edges, a.w, gamma, sigma, (float2*)Ut, Yh, alpha, kind, m, ld,
               part, ctl);
         else
