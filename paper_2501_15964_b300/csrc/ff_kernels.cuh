@@ -102,7 +102,7 @@ __device__ __forceinline__ uint8_t ff_edge_outputs(const ff (&y)[CH][4], ff r, f
 // Evaluation edge pass (as k_edge_eval) in float-float: y, ||y||, kind, Pi(y) ->
 // Ut, yhat -> Yh, alpha; accumulates sum_l h_l and the number of outside edges.
 template <int LANES, int CH, typename Tc>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, CH <= 2 ? 4 : 1)
 k_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
                const int2* __restrict__ edges, const double* __restrict__ w, double gamma,
                double sigma, float2* __restrict__ Ut, Tc* __restrict__ Yh, Tc* __restrict__ alpha,
@@ -114,9 +114,17 @@ k_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
   const ff sg = d2ff(sigma), gm = d2ff(gamma);
   ff hacc = {0.0f, 0.0f};
   int nout = 0;
+  // the next edge's endpoints and weight are loaded one edge ahead, so that the
+  // row loads of an edge wait on one round trip to memory instead of two
+  int2 ij_n = g0 < m ? edges[g0] : make_int2(0, 0);
+  double w_n = g0 < m ? w[g0] : 0.0;
   for (int64_t e = g0; e < m; e += ng) {
-    const int2 ij = edges[e];
-    const ff r = ff_mul(gm, d2ff(w[e]));
+    const int2 ij = ij_n;
+    const ff r = ff_mul(gm, d2ff(w_n));
+    if (e + ng < m) {
+      ij_n = edges[e + ng];
+      w_n = w[e + ng];
+    }
     ff xi[CH][4], xj[CH][4], y[CH][4];
     ff_row_load<LANES, CH>(XF + (int64_t)ij.x * ld, ld, lane, xi);
     ff_row_load<LANES, CH>(XF + (int64_t)ij.y * ld, ld, lane, xj);
@@ -160,9 +168,17 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
   const ff sg = d2ff(sigma), gm = d2ff(gamma);
   ff racc = {0.0f, 0.0f}, pacc = {0.0f, 0.0f}, hacc = {0.0f, 0.0f};  // ||res||^2, sum r||bx||, sum h
   int nout = 0;
+  // the next edge's endpoints and weight are loaded one edge ahead, so that the
+  // row loads of an edge wait on one round trip to memory instead of two
+  int2 ij_n = g0 < m ? edges[g0] : make_int2(0, 0);
+  double w_n = g0 < m ? w[g0] : 0.0;
   for (int64_t e = g0; e < m; e += ng) {
-    const int2 ij = edges[e];
-    const ff r = ff_mul(gm, d2ff(w[e]));
+    const int2 ij = ij_n;
+    const ff r = ff_mul(gm, d2ff(w_n));
+    if (e + ng < m) {
+      ij_n = edges[e + ng];
+      w_n = w[e + ng];
+    }
     // u and bx are the edge's rows; v = u + bx and y = u + sigma bx are formed
     // from them where they are needed (by the same operations each time, so
     // with the same values), and the launch bounds ask for two resident blocks
@@ -248,7 +264,10 @@ k_node_grad_ff(const double* __restrict__ X, const double* __restrict__ Ap,
   // The chain of dependent scalar loads in front of a node's gathers (its index
   // in the visiting order, then its row range) is pipelined across the group's
   // nodes: the range of the next node and the index of the one after it are
-  // loaded while this node is processed.
+  // loaded while this node is processed. (Loading the record batches one batch
+  // ahead as well, as the operator does, needed 6 more registers and took 500
+  // against 487 us: at one quad per lane this kernel is bound by the three
+  // resident blocks per SM that 80 registers allow.)
   auto node_of = [&](int64_t gi) -> int64_t {
     return gi < n ? (ord ? (int64_t)ord[gi] : gi) : 0;
   };

@@ -212,7 +212,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUten
   float* sA = reinterpret_cast<float*>(base);               // [nkb][2][128 x 32]
   float* sB = sA + (size_t)nkb * 2 * kTileFloats;          // [nstages][2][128 x 32]
   float* snorm = sB + (size_t)nstages * 2 * kTileFloats;    // [2][128] column norms
-  float* sdist = snorm + 2 * kBN;                             // [256][32] one chunk per thread
+  float* sdist = snorm + 2 * kBN;                             // [32][256] one chunk per thread
   uint64_t* full = reinterpret_cast<uint64_t*>(sdist + 256 * 32 + 4);
   uint64_t* empty = full + nstages;
   uint64_t* tfull = empty + nstages;        // [kAccBufs]
@@ -362,7 +362,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUten
     volatile int* stop = abort_flag + 1;  // the epilogue's common decision to stop
     if (et < kBN) snorm[et] = nbf[et];    // tile 0
     asm volatile("bar.sync 1, 256;" ::: "memory");
-    float* sd = sdist + et * 32;  // this thread's staging row (XOR-swizzled columns)
+    float* sdc = sdist + et;  // this thread's staging column ([32][256] layout)
     for (int t = 0; t < ntiles; ++t) {
       const int b = t % kAccBufs;
       const float pf = (t + 1 < ntiles && et < kBN) ? nbf[(int64_t)(t + 1) * kBN + et] : 0.0f;
@@ -378,14 +378,15 @@ k_knn_tc(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUten
           float v[32];
           tc_ld_32cols(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN + c * 32),
                        v);
-          // D~ for the 32 columns, staged in this thread's shared-memory row
-          // (columns XOR-swizzled by lane), and a mask of those below the current
-          // threshold; the (rare) insertions then run from one copy of the
-          // insertion code, which keeps the loop small enough for the
-          // instruction cache and costs the warp only as many passes as its
-          // busiest lane has insertions
+          // D~ for the 32 columns in registers and their minimum; only when that
+          // minimum is below the current threshold (rare once the list holds
+          // near neighbours) are the distances staged in shared memory (column
+          // j of this thread at sdc[256 j]: fixed offsets, no bank conflicts)
+          // and the insertions run from one copy of the insertion code, which
+          // keeps the loop small enough for the instruction cache and costs the
+          // warp only as many passes as its busiest lane has insertions
           const float4* sn4 = reinterpret_cast<const float4*>(sn + c * 32);
-          uint32_t msk = 0u;
+          float mn = INFINITY;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float4 s4 = sn4[q];
@@ -393,18 +394,25 @@ k_knn_tc(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUten
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int jj = 4 * q + e;
-              const float dt = fmaf(-2.0f, v[jj], ni + sv4[e]);
-              sd[jj ^ lane] = dt;
-              msk |= (dt < thr ? 1u : 0u) << jj;
+              v[jj] = fmaf(-2.0f, v[jj], ni + sv4[e]);
+              mn = fminf(mn, v[jj]);
             }
           }
-          const int cb = col0 + c * 32;
-          if (gi >= cb && gi < cb + 32) msk &= ~(1u << (gi - cb));
-          while (msk) {
-            const int jj = __ffs(msk) - 1;
-            msk &= msk - 1u;
-            const float dt = sd[jj ^ lane];
-            if (dt < thr) list_insert<KP>(ld, lj, thr, dt, cb + jj);
+          if (mn < thr) {
+            uint32_t msk = 0u;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              sdc[jj * 256] = v[jj];
+              msk |= (v[jj] < thr ? 1u : 0u) << jj;
+            }
+            const int cb = col0 + c * 32;
+            if (gi >= cb && gi < cb + 32) msk &= ~(1u << (gi - cb));
+            while (msk) {
+              const int jj = __ffs(msk) - 1;
+              msk &= msk - 1u;
+              const float dt = sdc[jj * 256];
+              if (dt < thr) list_insert<KP>(ld, lj, thr, dt, cb + jj);
+            }
           }
         }
         tc_fence_before();
@@ -502,7 +510,7 @@ int knn_candidates_tc(Ctx* c, const float* At, int ldf, int64_t n, int d, int Kp
   const size_t abytes = (size_t)nkb * 2 * kTileFloats * 4;
   const size_t stage = (size_t)2 * kTileFloats * 4;
   // shared memory: alignment slack, A (resident), the B stage ring, column norms,
-  // the epilogue's staging rows and the barriers; as many stages (2..4) as fit
+  // the epilogue's staging buffer and the barriers; as many stages (2..4) as fit
   int optin = 0;
   CCM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   const size_t fixed = 1024 + (2 * kBN + 256 * 32 + 4) * 4 + 256;

@@ -118,6 +118,35 @@ k_kkt_node(const double* __restrict__ X, const double* __restrict__ Ap,
   }
 }
 
+// k_kkt_node with the element arithmetic in float-float on the FP32 pipe (the
+// float64 form occupies B300's narrow FP64 pipe: four float64 operations per
+// element against 24 bytes of loads). Quads of four elements per thread.
+__global__ void __launch_bounds__(256)
+k_kkt_node_ff(const double* __restrict__ X, const double* __restrict__ Ap,
+              const double* __restrict__ G, int64_t total, double* partials, Ctl* ctl) {
+  ff s_ab = {0.0f, 0.0f}, s_bb = {0.0f, 0.0f};  // <A, B^T U>, ||B^T U||^2 (bb unnormalised)
+  for (int64_t q4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; q4 < total;
+       q4 += (int64_t)gridDim.x * blockDim.x * 4) {
+    double x[4], a[4], g[4];
+    Vec4<double>::load(X + q4, x);
+    Vec4<double>::load(Ap + q4, a);
+    Vec4<double>::load(G + q4, g);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const ff af = d2ff(a[k]);
+      const ff btu = ff_sub(d2ff(g[k]), ff_sub(d2ff(x[k]), af));
+      s_ab = ff_add(s_ab, ff_mul(btu, af));
+      ff_sqr_acc(s_bb, btu);
+    }
+  }
+  double acc[2] = {ff2d(s_ab), ff2d(ff_norm(s_bb))};
+  double tot[2];
+  if (grid_reduce<2>(acc, partials, &ctl->counter[C_KKT_N], tot) && threadIdx.x == 0) {
+    ctl->kkt[2] = tot[0];
+    ctl->kkt[3] = tot[1];
+  }
+}
+
 __global__ void k_sumsq(const double* __restrict__ v, int64_t total, double* partials,
                         Ctl* ctl) {
   double acc[1] = {0.0};
@@ -624,7 +653,10 @@ struct GridEngine {
         CCM_COUNT(c);
         edge_ready = true;
         edge_sigma = sigma;
-        k_kkt_node<<<b_elem, threads, 0, s>>>(X, Ap, G, nl, part, ctl);
+        if (FF)
+          k_kkt_node_ff<<<b_quad, threads, 0, s>>>(X, Ap, G, nl, part, ctl);
+        else
+          k_kkt_node<<<b_elem, threads, 0, s>>>(X, Ap, G, nl, part, ctl);
         CCM_COUNT(c);
         CCM_CUDA(cudaGetLastError());
         CCM_TRY(readback());

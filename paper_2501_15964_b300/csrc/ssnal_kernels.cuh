@@ -354,6 +354,24 @@ struct alignas(2 * sizeof(Tc)) IncMeta {
   Tc c, mo;
 };
 
+// Dot products of the CG kernels: float32 products summed in float-float
+// (two-product and two-sum on the FP32 pipe); float64 vectors sum plainly.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  // s + e += x with the rounding error of s + x kept in e (Knuth's two-sum)
+  const float t = s + x;
+  const float bp = t - s;
+  e += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+__device__ __forceinline__ void dot_acc(float& s, float& e, float a, float b) {
+  const float p = a * b;
+  e += fmaf(a, b, -p);  // exact product error (fused multiply-add)
+  two_sum_acc(s, e, p);
+}
+__device__ __forceinline__ void dot_acc(double& s, double& e, double a, double b) {
+  s = fma(a, b, s);
+}
+
 // R = -G, Dx = 0; rr = <R,R>, rz = <R, Minv R>; tol2 = eta^2 rr. Also packs the
 // incidence coefficients (meta may be null).
 template <typename Tc>
@@ -363,17 +381,28 @@ k_cg_init(const double* __restrict__ G, const Tc* __restrict__ Minv, Tc* __restr
           const int2* __restrict__ inc, const uint8_t* __restrict__ kind,
           const Tc* __restrict__ alpha, IncMeta<Tc>* __restrict__ meta, int64_t ninc,
           double* partials, Ctl* ctl) {
-  double acc[2] = {0.0, 0.0};
+  // rr = <R, R>, rz = <R, Minv R> as in k_cg_update (float-float sums of the
+  // operator-precision products; one row index per quad: ld is a multiple of 4)
+  Tc rr_t = (Tc)0, rr_e = (Tc)0, rz_t = (Tc)0, rz_e = (Tc)0;
   const int64_t total = n * ld;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
-    Tc r = (Tc)(-G[t]);
-    R[t] = r;
-    Dx[t] = (Tc)0;
-    double rd = (double)r;
-    acc[0] += rd * rd;
-    acc[1] += rd * rd * (double)Minv[t / ld];
+  for (int64_t t4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; t4 < total;
+       t4 += stride * 4) {
+    double g[4];
+    Vec4<double>::load(G + t4, g);
+    const Tc mi = Minv[t4 / ld];
+    Tc r[4], z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      r[k] = (Tc)(-g[k]);
+      z[k] = (Tc)0;
+      dot_acc(rr_t, rr_e, r[k], r[k]);
+      dot_acc(rz_t, rz_e, mi * r[k], r[k]);
+    }
+    Vec4<Tc>::store(R + t4, r);
+    Vec4<Tc>::store(Dx + t4, z);
   }
+  double acc[2] = {(double)rr_t + (double)rr_e, (double)rz_t + (double)rz_e};
   if (meta)
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ninc; t += stride) {
       const int2 eo = inc[t];
@@ -416,31 +445,6 @@ __device__ __forceinline__ void cg_set_alpha(Ctl* ctl, double delta) {
   }
 }
 
-// W = D u + sigma B^T P B u with u = Minv R (D = I, or the diagonal Dg);
-// delta = <W, u>. Node-parallel pull over the CSR of B^T: a group of LANES
-// threads owns node i and visits its incidences in increasing edge id,
-// gathering the other endpoint's R row (and the yhat / mask / s row of the edge
-// for the kinds that have one). Like k_node_grad, the group reads its node's
-// incidence records and packed coefficients LANES at a time (one per lane) and
-// keeps kNB gathered rows in flight; the terms are still added in edge-id
-// order. Used for short rows and the adjoint; k_cg_matvec_ring stages long rows
-// through shared memory. The dot product <W, u> is accumulated exactly in
-// float-float form (two_prod / two_sum) per lane, then in float64.
-__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
-  // s + e += x with the rounding error of s + x kept in e (Knuth's two-sum)
-  const float t = s + x;
-  const float bp = t - s;
-  e += (s - (t - bp)) + (x - bp);
-  s = t;
-}
-__device__ __forceinline__ void dot_acc(float& s, float& e, float a, float b) {
-  const float p = a * b;
-  e += fmaf(a, b, -p);  // exact product error (fused multiply-add)
-  two_sum_acc(s, e, p);
-}
-__device__ __forceinline__ void dot_acc(double& s, double& e, double a, double b) {
-  s = fma(a, b, s);
-}
 
 template <int LANES, int CH, typename Tc>
 __device__ __forceinline__ void matvec_term(Tc c, Tc mo, const Tc (&u)[CH][4], const Tc (&v0)[CH][4],
@@ -488,6 +492,16 @@ __device__ __forceinline__ void matvec_term(Tc c, Tc mo, const Tc (&u)[CH][4], c
   }
 }
 
+// W = D u + sigma B^T P B u with u = Minv R (D = I, or the diagonal Dg);
+// delta = <W, u>. Node-parallel pull over the CSR of B^T: a group of LANES
+// threads owns node i and visits its incidences in increasing edge id,
+// gathering the other endpoint's R row (and the yhat / mask / s row of the edge
+// for the kinds that have one). Like k_node_grad, the group reads its node's
+// incidence records and packed coefficients LANES at a time (one per lane) and
+// keeps kNB gathered rows in flight; the terms are still added in edge-id
+// order. Used for short rows and the adjoint; k_cg_matvec_ring stages long rows
+// through shared memory. The dot product <W, u> is accumulated exactly in
+// float-float form (two_prod / two_sum) per lane, then in float64.
 template <int LANES, int CH, typename Tc>
 __global__ void __launch_bounds__(256)
 k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __restrict__ Dg,
@@ -502,8 +516,40 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
   const int64_t ng = (int64_t)gridDim.x * blockDim.x / LANES;
   const Tc sg = (Tc)sigma;
   Tc dot = (Tc)0, dot_e = (Tc)0;  // <W, u> over this thread's elements, float-float
+  // Dependent loads are pipelined across the group's nodes and record batches:
+  // the next node's row range (and the index of the one after it) is loaded at
+  // the start of a node, and every batch of LANES incidence records is loaded
+  // one batch ahead (the first batch of the next node during the last batch of
+  // this one), so the row gathers wait on at most one round trip to memory.
+  auto node_of = [&](int64_t gi) -> int64_t {
+    return gi < n ? (ord ? (int64_t)ord[gi] : gi) : 0;
+  };
+  auto records = [&](int64_t pb, int64_t pe, int2& rec, IncMeta<Tc>& mm) {
+    rec = make_int2(0, 0);
+    mm.c = (Tc)0;
+    mm.mo = (Tc)0;
+    if (pb + lane < pe) {
+      rec = inc[pb + lane];
+      mm = meta[pb + lane];
+    }
+  };
+  int64_t i_cur = node_of(g0);
+  int64_t b_cur = g0 < n ? off[i_cur] : 0, e_cur = g0 < n ? off[i_cur + 1] : 0;
+  int64_t i_nxt = node_of(g0 + ng);
+  int2 rec;
+  IncMeta<Tc> mm;
+  records(b_cur, e_cur, rec, mm);
   for (int64_t gi = g0; gi < n; gi += ng) {
-    const int64_t i = ord ? (int64_t)ord[gi] : gi;  // visiting order (see degree_order)
+    const int64_t i = i_cur, b = b_cur, eend = e_cur;
+    int64_t bn = 0, en = 0;  // the next node's row range
+    if (gi + ng < n) {
+      bn = off[i_nxt];
+      en = off[i_nxt + 1];
+    }
+    i_cur = i_nxt;
+    i_nxt = node_of(gi + 2 * ng);
+    b_cur = bn;
+    e_cur = en;
     Tc u[CH][4], accv[CH][4];
     const Tc mi = Minv[i];
     row_load<LANES, CH>(R + i * ld, ld, lane, u);
@@ -514,17 +560,15 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
         u[c][k] *= mi;
         accv[c][k] = (Tc)0;
       }
-    const int64_t b = off[i], eend = off[i + 1];
+    if (eend <= b) records(bn, en, rec, mm);  // no batch of this node prefetches the next
     for (int64_t base = b; base < eend; base += LANES) {
       const int nb = (int)(eend - base < (int64_t)LANES ? eend - base : (int64_t)LANES);
-      int2 rec = make_int2(0, 0);
-      IncMeta<Tc> mm;
-      mm.c = (Tc)0;
-      mm.mo = (Tc)0;
-      if (lane < nb) {
-        rec = inc[base + lane];
-        mm = meta[base + lane];
-      }
+      int2 rec_n;
+      IncMeta<Tc> mm_n;
+      if (base + LANES < eend)
+        records(base + LANES, eend, rec_n, mm_n);
+      else
+        records(bn, en, rec_n, mm_n);
       for (int j = 0; j < nb; j += NB) {
         Tc v0[NB][CH][4], yh[NB][CH][4];
         Tc cs[NB], mos[NB];
@@ -556,6 +600,8 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
         for (int kk = 0; kk < NB; ++kk)
           matvec_term<LANES, CH, Tc>(cs[kk], mos[kk], u, v0[kk], yh[kk], accv, mask);
       }
+      rec = rec_n;
+      mm = mm_n;
     }
     const Tc di = Dg ? Dg[i] : (Tc)1;  // diagonal term (1 for V; cluster sizes for the adjoint)
 #pragma unroll
