@@ -80,6 +80,10 @@ typedef struct {
                              shapes (lanes x quads per row) on a sample of a batch of
                              >= 8 problems and caches the fastest per context, d,
                              precision and mean degree; 0: default shape unless cached */
+  int32_t coarse;         /* 1: q = 2 grid-engine Newton steps add a coarse correction to
+                             the Jacobi preconditioner, one unknown per component of
+                             >= 16 nodes of the strong edges (inside, or outside with
+                             tr(P_l)/d >= 1/2; the 224 largest); 0 (default): Jacobi only */
   const double* X0;       /* optional device n x d warm start for the first gamma, or NULL */
   const double* U0;       /* optional device m x d multipliers for the first gamma (must
                              satisfy ||u_l|| <= gamma_1 w_l), or NULL */
@@ -107,6 +111,8 @@ typedef struct {
   int64_t kernel_launches;   /* all kernels the last ccm_solve_path call launched */
   int32_t block_lanes;       /* block engine (last block-engine call): lanes per row group */
   int32_t block_quads;       /* ... and quads per lane (the autotuned or cached shape) */
+  int32_t coarse_steps;      /* Newton steps that used the coarse correction */
+  int32_t coarse_max_aggregates; /* largest number of coarse unknowns of those steps */
 } ccm_profile;
 
 /* Total number of kernels launched through this context since ccm_create. */

@@ -29,7 +29,7 @@ class Options(C.Structure):
         ("sigma0", C.c_double), ("sigma_max", C.c_double),
         ("max_outer", C.c_int32), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
         ("precision", C.c_int32), ("engine", C.c_int32), ("profile", C.c_int32),
-        ("relabel", C.c_int32), ("autotune", C.c_int32),
+        ("relabel", C.c_int32), ("autotune", C.c_int32), ("coarse", C.c_int32),
         ("X0", C.c_void_p), ("U0", C.c_void_p),
     ]
 
@@ -49,7 +49,8 @@ class Stats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("matvec_launches", C.c_int64), ("matvec_ms_total", C.c_double),
                 ("matvec_bytes_total", C.c_double), ("kernel_launches", C.c_int64),
-                ("block_lanes", C.c_int32), ("block_quads", C.c_int32)]
+                ("block_lanes", C.c_int32), ("block_quads", C.c_int32),
+                ("coarse_steps", C.c_int32), ("coarse_max_aggregates", C.c_int32)]
 
 
 class GraphInfo(C.Structure):

@@ -149,7 +149,8 @@ def last_profile(ctx: Context | None = None) -> dict:
     check(load_library().ccm_last_profile(ctx.handle, C.byref(p)))
     return {"matvec_launches": p.matvec_launches, "matvec_ms_total": p.matvec_ms_total,
             "matvec_bytes_total": p.matvec_bytes_total, "kernel_launches": p.kernel_launches,
-            "block_lanes": p.block_lanes, "block_quads": p.block_quads}
+            "block_lanes": p.block_lanes, "block_quads": p.block_quads,
+            "coarse_steps": p.coarse_steps, "coarse_max_aggregates": p.coarse_max_aggregates}
 
 
 def last_graph_info(ctx: Context | None = None) -> dict:

@@ -160,6 +160,7 @@ void ccm_default_options(ccm_options* o) {
   o->profile = 0;
   o->relabel = 1;
   o->autotune = 1;
+  o->coarse = 0;
   o->X0 = nullptr;
   o->U0 = nullptr;
 }

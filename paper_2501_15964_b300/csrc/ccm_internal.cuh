@@ -45,7 +45,8 @@ enum Slot : int {
   S_U, S_UT, S_YH, S_ALPHA, S_KIND, S_EDGES, S_CSR_OFF, S_CSR_INC, S_PART, S_CTRL,
   S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
   S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3, S_META, S_WPART, S_VJPF, S_ADMM,
-  S_XF0, S_XF1, S_KNN, S_REORD, S_ORDER, S_ORDER_TMP, S_COUNT
+  S_XF0, S_XF1, S_KNN, S_REORD, S_ORDER, S_ORDER_TMP, S_CO_PARENT, S_CO_AGG, S_CO_A, S_CO_AINV,
+  S_CO_YZ, S_CO_U, S_CO_ONES, S_COUNT
 };
 
 // Autotuned group shape of the block engine for one (d, precision, degree bucket).

@@ -11,6 +11,7 @@
 #include <cstdlib>
 
 #include "ccm_internal.cuh"
+#include "coarse.cuh"
 #include "solve_common.cuh"
 #include "ff_kernels.cuh"
 #include "ring_kernels.cuh"
@@ -341,6 +342,13 @@ int build_csr(Ctx* c, const int2* edges, int64_t m, int64_t n, int64_t** off_out
   return CCM_OK;
 }
 
+template <typename Tc>
+__global__ void k_fill_one(Tc* __restrict__ v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (Tc)1;
+}
+
 // ---------------------------------------------------------------- engine
 template <int L, int CH, typename Tc>
 struct GridEngine {
@@ -388,6 +396,10 @@ struct GridEngine {
     // in float-float (ff_kernels.cuh); U / Pi(y) rows are then float-float rows
     // (same 8 bytes per element) and X has a float-float mirror
     const bool FF = a.q == 2 && sizeof(Tc) == 4;
+    // two-level preconditioner (q = 2): its vectors are taken at first use
+    const bool use_coarse = a.opt.coarse != 0 && a.q == 2;
+    Tc* Uco = nullptr;   // U = M^-1 R
+    Tc* ones = nullptr;  // unit Jacobi scalars for the operator on U
     float2 *XFa = nullptr, *XFb = nullptr;
     if (FF) {
       CCM_TRY(get(S_XF0, nl * 8, &p)); XFa = (float2*)p;
@@ -574,18 +586,38 @@ struct GridEngine {
           if (gn / scale <= eps_in) break;
           const double gr = gn / scale;
           const double eta = std::min(0.1, std::max(tc_floor, std::sqrt(gr)));
-          k_cg_init<Tc><<<b_elem, threads, 0, s>>>(G, Minv, R, Dx, n, ld, eta, a.opt.max_cg,
-                                                   inc, kind, alpha, meta, 2 * m, part, ctl);
+          // two-level preconditioner (options.coarse): when the strong edges form
+          // aggregates, the CG runs on U = M^-1 R (coarse.cu) with unit Jacobi scalars
+          CoarsePlan<Tc> cp;
+          if (use_coarse) {
+            CCM_TRY(coarse_build<Tc>(c, edges, kind, alpha, n, m, sigma, d, ld, cp, s));
+            if (cp.K > 0) {
+              if (!Uco) {
+                CCM_TRY(get(S_CO_U, nl * sizeof(Tc), &p)); Uco = (Tc*)p;
+                CCM_TRY(get(S_CO_ONES, n * sizeof(Tc), &p)); ones = (Tc*)p;
+                k_fill_one<Tc><<<nb(n), threads, 0, s>>>(ones, n);
+                CCM_COUNT(c);
+              }
+              profile.coarse_steps += 1;
+              profile.coarse_max_aggregates = std::max(profile.coarse_max_aggregates, cp.K);
+            }
+          }
+          const bool co = cp.K > 0;
+          k_cg_init<Tc><<<b_elem, threads, 0, s>>>(G, co ? ones : Minv, R, Dx, n, ld, eta,
+                                                   a.opt.max_cg, inc, kind, alpha, meta, 2 * m,
+                                                   part, ctl);
           CCM_COUNT(c);
           CCM_CUDA(cudaGetLastError());
           int it_before = 0;
           for (int chunk = 0; chunk * CHUNK < a.opt.max_cg; ++chunk) {
             for (int k = 0; k < CHUNK; ++k) {
+              if (co) CCM_TRY(coarse_precondition<Tc>(c, cp, R, Minv, Uco, n, ld, part, ctl, s));
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k], s));
-              CCM_TRY(launch_matvec<L, CH, Tc>(c, R, Minv, nullptr, W, Yh, meta, off, inc, rp,
-                                                sigma, n, ld, part, ctl, s));
+              CCM_TRY(launch_matvec<L, CH, Tc>(c, co ? Uco : R, co ? ones : Minv, nullptr, W, Yh,
+                                                meta, off, inc, rp, sigma, n, ld, part, ctl, s));
               if (prof) CCM_CUDA(cudaEventRecord(ev[2 * k + 1], s));
-              k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, P, Sv, R, W, Minv, n, ld, part, ctl);
+              k_cg_update<Tc><<<b_quad, threads, 0, s>>>(Dx, P, Sv, R, W, Minv, n, ld, part, ctl,
+                                                         co ? Uco : nullptr);
               CCM_COUNT(c);
             }
             CCM_CUDA(cudaGetLastError());

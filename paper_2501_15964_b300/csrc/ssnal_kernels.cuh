@@ -621,12 +621,14 @@ k_cg_matvec(const Tc* __restrict__ R, const Tc* __restrict__ Minv, const Tc* __r
 
 // P = u + beta P, S = W + beta S (u = Minv R; P = u, S = W on the first
 // iteration), Dx += alpha P, R -= alpha S; rz = <R, Minv R>, rr = <R,R>;
-// beta and the stop test for the next iteration.
+// beta and the stop test for the next iteration. With the coarse correction
+// (Uc non-null) u = Uc = M^-1 R was formed before the operator, and rz and beta
+// of the next iteration come from that step (coarse_precondition), not here.
 template <typename Tc>
 __global__ void __launch_bounds__(256)
 k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __restrict__ R,
             const Tc* __restrict__ W, const Tc* __restrict__ Minv, int64_t n, int ld,
-            double* partials, Ctl* ctl) {
+            double* partials, Ctl* ctl, const Tc* __restrict__ Uc = nullptr) {
   if (!ctl->cg.active) return;
   const Tc al = (Tc)ctl->cg.alpha;
   const Tc be = (Tc)ctl->cg.beta;
@@ -644,10 +646,17 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
     Vec4<Tc>::load(R + t4, r);
     Vec4<Tc>::load(W + t4, w);
     const Tc mi = Minv[t4 / ld];
+    Tc u[4];
+    if (Uc) {
+      Vec4<Tc>::load(Uc + t4, u);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) u[k] = mi * r[k];
+    }
     if (first) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        p[k] = mi * r[k];
+        p[k] = u[k];
         sv[k] = w[k];
       }
     } else {
@@ -655,7 +664,7 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
       Vec4<Tc>::load(S + t4, sv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        p[k] = mi * r[k] + be * p[k];
+        p[k] = u[k] + be * p[k];
         sv[k] = w[k] + be * sv[k];
       }
     }
@@ -676,10 +685,12 @@ k_cg_update(Tc* __restrict__ Dx, Tc* __restrict__ P, Tc* __restrict__ S, Tc* __r
   if (grid_reduce<2>(acc, partials, &ctl->counter[C_UPD], tot) && threadIdx.x == 0) {
     CgCtl& c = ctl->cg;
     c.it += 1;
-    c.beta = (c.rz > 0.0) ? tot[0] / c.rz : 0.0;
-    c.rz = tot[0];
+    if (!Uc) {
+      c.beta = (c.rz > 0.0) ? tot[0] / c.rz : 0.0;
+      c.rz = tot[0];
+    }
     c.rr = tot[1];
-    if (!(tot[1] > c.tol2) || c.it >= c.maxit || !isfinite(tot[1]) || !(tot[0] > 0.0))
+    if (!(tot[1] > c.tol2) || c.it >= c.maxit || !isfinite(tot[1]) || (!Uc && !(tot[0] > 0.0)))
       c.active = 0;
   }
 }
