@@ -210,15 +210,20 @@ k_kkt_edge_eval_ff(const float2* __restrict__ XF, const float2* __restrict__ U,
     const ff rv = sv.h > 0.0f ? ff_rsqrt(sv) : ff{0.0f, 0.0f};
     const ff nsh = ff_le(ff_mul(sv, rv), r) ? ff{0.0f, 0.0f}
                                             : ff_sub(ff_mul(r, rv), ff{1.0f, 0.0f});  // -shrink
-    // residual bx - shrink v: its norm only enters eta_P, so its square is summed
-    // in float32 from the float-float difference
+    // residual bx - shrink v: its norm only enters eta_P, so the residual is
+    // formed to float32 accuracy: the high words in one fused multiply-add
+    // (rounded once, so a residual far below |bx| keeps its relative accuracy)
+    // plus the low-word terms in float32 (absolute error about 2^-46 |bx|, the
+    // product of the two low words dropped), and its square summed in float32
     float sres = 0.0f;
 #pragma unroll
     for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const ff res = ff_add(bx[c][k], ff_mul(ff_add(u[c][k], bx[c][k]), nsh));
-        sres = fmaf(res.h, res.h, sres);
+        const ff v = ff_add(u[c][k], bx[c][k]);
+        const float lo = bx[c][k].l + fmaf(nsh.h, v.l, nsh.l * v.h);
+        const float res = fmaf(nsh.h, v.h, bx[c][k].h) + lo;
+        sres = fmaf(res, res, sres);
       }
     racc = ff_add(racc, ff{sres, 0.0f});
     // y = u + sigma bx in place of u
