@@ -170,6 +170,11 @@ int ccm_build_graph(ccm_ctx* ctx, const double* A, int64_t n, int32_t d, int32_t
  * cluster's smallest node index; an edge is fused when the float64 squared
  * distance of its endpoints, summed in feature order without FMA, is <= 1e-12);
  * U: T x m x d float64 or NULL (final multipliers); stats: HOST array of T or NULL.
+ * X and labels may be device or host memory (pinned host memory recommended):
+ * for host X the path runs on a device staging buffer held by the context, and
+ * each gamma's X is copied to the host on the context's copy stream while the
+ * next gamma solves; host labels are copied after the path. The call returns
+ * after every copy has landed. U must be device memory (CCM_ERR_INVALID_ARG).
  * For q = 1, eta_p uses prox of r_l ||.||_1 (soft threshold) and f_p r_l ||.||_1;
  * for q = inf, prox of r_l ||.||_inf (identity minus the l1-ball projection) and
  * r_l ||.||_inf.

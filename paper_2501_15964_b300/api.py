@@ -76,8 +76,13 @@ def build_graph(A: torch.Tensor, k: int, phi: float = 0.0, ctx: Context | None =
 
 def solve_path(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U: bool = False,
                labels_out: bool = True, ctx: Context | None = None, raise_on_cap=False,
+               X_out: torch.Tensor | None = None, labels_host: torch.Tensor | None = None,
                **options):
     """X*(gamma_t) for every gamma (see ccm_solve_path).
+
+    X_out / labels_host: optional host tensors (float64 [T,n,d], int32 [T,n];
+    pinned memory lets the library copy each gamma's X while the next one solves)
+    that receive the outputs instead of new device tensors.
 
     Returns (X [T,n,d] float64, labels [T,n] int32 or None, U [T,m,d] or None,
     stats: list of dicts)."""
@@ -89,8 +94,20 @@ def solve_path(A, edges, w, gammas, tol: float = 1e-6, q: int = 2, return_U: boo
     g = [float(x) for x in gammas]
     T = len(g)
     ctx = ctx or default_context(A.device.index)
-    X = torch.empty((T, n, d), dtype=torch.float64, device=A.device)
-    lab = torch.empty((T, n), dtype=torch.int32, device=A.device) if labels_out else None
+    if X_out is not None:
+        if (X_out.device.type != "cpu" or X_out.dtype != torch.float64
+                or tuple(X_out.shape) != (T, n, d) or not X_out.is_contiguous()):
+            raise ValueError("X_out must be a contiguous float64 CPU tensor of shape (T, n, d)")
+        X = X_out
+    else:
+        X = torch.empty((T, n, d), dtype=torch.float64, device=A.device)
+    if labels_host is not None:
+        if (labels_host.device.type != "cpu" or labels_host.dtype != torch.int32
+                or tuple(labels_host.shape) != (T, n) or not labels_host.is_contiguous()):
+            raise ValueError("labels_host must be a contiguous int32 CPU tensor of shape (T, n)")
+        lab = labels_host
+    else:
+        lab = torch.empty((T, n), dtype=torch.int32, device=A.device) if labels_out else None
     U = torch.empty((T, m, d), dtype=torch.float64, device=A.device) if return_U else None
     stats = (Stats * T)()
     garr = (C.c_double * T)(*g)

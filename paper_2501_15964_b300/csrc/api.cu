@@ -199,6 +199,8 @@ void ccm_destroy(ccm_ctx* x) {
     if (x->c.slot_ptr[s]) cudaFree(x->c.slot_ptr[s]);
   if (x->c.host_pinned) cudaFreeHost(x->c.host_pinned);
   for (auto ev : x->c.ev_pool) cudaEventDestroy(ev);
+  if (x->c.copy_event) cudaEventDestroy(x->c.copy_event);
+  if (x->c.copy_stream) cudaStreamDestroy(x->c.copy_stream);
   delete x;
 }
 

@@ -46,7 +46,7 @@ enum Slot : int {
   S_SCRATCH0, S_SCRATCH1, S_SCRATCH2, S_SCRATCH3, S_SCRATCH4, S_SCRATCH5,
   S_SCRATCH6, S_SCRATCH7, S_BATCH0, S_BATCH1, S_BATCH2, S_BATCH3, S_META, S_WPART, S_VJPF, S_ADMM,
   S_XF0, S_XF1, S_KNN, S_REORD, S_ORDER, S_ORDER_TMP, S_CO_PARENT, S_CO_AGG, S_CO_A, S_CO_AINV,
-  S_CO_YZ, S_CO_U, S_CO_ONES, S_COUNT
+  S_CO_YZ, S_CO_U, S_CO_ONES, S_XSTAGE, S_LSTAGE, S_COUNT
 };
 
 // Autotuned group shape of the block engine for one (d, precision, degree bucket).
@@ -61,6 +61,8 @@ struct Ctx {
   void* slot_ptr[S_COUNT] = {};
   size_t slot_size[S_COUNT] = {};
   void* host_pinned = nullptr;   // small pinned buffer for scalar read-back
+  cudaStream_t copy_stream = nullptr;  // device-to-host output copies (created at first use)
+  cudaEvent_t copy_event = nullptr;
   size_t host_pinned_size = 0;
   std::vector<cudaEvent_t> ev_pool;
   ccm_profile last_profile = {};

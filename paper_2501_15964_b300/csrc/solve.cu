@@ -349,6 +349,16 @@ __global__ void k_fill_one(Tc* __restrict__ v, int64_t n) {
     v[i] = (Tc)1;
 }
 
+// Host memory (pinned or pageable) as seen by the CUDA runtime.
+static bool is_host_memory(const void* ptr) {
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
+}
+
 // ---------------------------------------------------------------- engine
 template <int L, int CH, typename Tc>
 struct GridEngine {
@@ -733,6 +743,12 @@ struct GridEngine {
       k_scatter_rows<<<nb(n * d), threads, 0, s>>>(X, a.Xout + (int64_t)t * n * d, n, d, ld,
                                                    a.perm);
       CCM_COUNT(c);
+      if (a.Xhost) {  // this gamma's X goes to the host while the next one solves
+        CCM_CUDA(cudaEventRecord(a.copy_event, s));
+        CCM_CUDA(cudaStreamWaitEvent(a.copy_stream, a.copy_event, 0));
+        CCM_CUDA(cudaMemcpyAsync(a.Xhost + (int64_t)t * n * d, a.Xout + (int64_t)t * n * d,
+                                 (size_t)n * d * 8, cudaMemcpyDeviceToHost, a.copy_stream));
+      }
       if (a.Uout && m > 0) {
         if (FF)
           k_unpad_rows_ff<<<nb(m * d), threads, 0, s>>>((const float2*)U,
@@ -821,10 +837,33 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
   }
   CCM_CUDA(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
+  // X and labels may be host memory: the path then runs on device staging
+  // buffers and the outputs are copied out (X of each gamma while the next one
+  // solves, on the context's copy stream); U must be device memory
+  const bool x_host = is_host_memory(X), l_host = labels && is_host_memory(labels);
+  if (U && is_host_memory(U)) {
+    set_error("ccm_solve_path: U must be device memory");
+    return CCM_ERR_INVALID_ARG;
+  }
   CCM_TRY(check_edges(c, (const int2*)edges, m, n, w, s));
+  double* Xd = X;
+  int32_t* Ld = labels;
+  void* p;
+  if (x_host) {
+    CCM_TRY(ws_get(c, S_XSTAGE, (size_t)T * n * d * 8, &p));
+    Xd = (double*)p;
+    if (!c->copy_stream) {
+      CCM_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+      CCM_CUDA(cudaEventCreateWithFlags(&c->copy_event, cudaEventDisableTiming));
+    }
+  }
+  if (l_host) {
+    CCM_TRY(ws_get(c, S_LSTAGE, (size_t)T * n * 4, &p));
+    Ld = (int32_t*)p;
+  }
   SolveArgs a;
   a.A = A; a.n = n; a.d = d; a.edges = edges; a.w = w; a.m = m;
-  a.gammas = gammas; a.T = T; a.tol = tol; a.opt = o; a.Xout = X; a.Uout = U;
+  a.gammas = gammas; a.T = T; a.tol = tol; a.opt = o; a.Xout = Xd; a.Uout = U;
   a.stats = stats; a.X0 = o.X0; a.U0 = o.U0; a.q = q;
   c->last_profile = ccm_profile{};
   const int64_t launches0 = c->launches;
@@ -841,10 +880,22 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     return CCM_ERR_UNSUPPORTED;
   }
   if (use_block) {
-    int st = solve_single_block(c, a, labels, s);
+    int st = solve_single_block(c, a, Ld, s);
+    if (st == CCM_OK || st == CCM_ERR_NOT_CONVERGED) {
+      if (x_host)
+        CCM_CUDA(cudaMemcpyAsync(X, Xd, (size_t)T * n * d * 8, cudaMemcpyDeviceToHost, s));
+      if (l_host)
+        CCM_CUDA(cudaMemcpyAsync(labels, Ld, (size_t)T * n * 4, cudaMemcpyDeviceToHost, s));
+      CCM_CUDA(cudaStreamSynchronize(s));
+    }
     c->last_profile.kernel_launches = c->launches - launches0;
     if (st == CCM_ERR_NOT_CONVERGED) set_error("ccm_solve_path: some gamma hit an iteration cap");
     return st;
+  }
+  if (x_host) {
+    a.Xhost = X;
+    a.copy_stream = c->copy_stream;
+    a.copy_event = c->copy_event;
   }
   // large graphs: solve with the nodes grouped by connected component (locality of
   // the gathers); the engine reads and writes the caller's arrays through the maps
@@ -857,14 +908,18 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     a.eperm = r.eperm;
   }
   int st = solve_grid(c, a, s);
+  // no copy into the caller's host memory may outlive the call
+  if (x_host) CCM_CUDA(cudaStreamSynchronize(c->copy_stream));
   if (st != CCM_OK && st != CCM_ERR_NOT_CONVERGED) return st;
   if (labels) {
     for (int t = 0; t < T; ++t) {
       int32_t nc = 0;
-      CCM_TRY(labels_device(c, X + (int64_t)t * n * d, d, n, d, (const int2*)edges, m,
-                            labels + (int64_t)t * n, stats ? &nc : nullptr, s));
+      CCM_TRY(labels_device(c, Xd + (int64_t)t * n * d, d, n, d, (const int2*)edges, m,
+                            Ld + (int64_t)t * n, stats ? &nc : nullptr, s));
       if (stats) stats[t].n_clusters = nc;
     }
+    if (l_host)
+      CCM_CUDA(cudaMemcpyAsync(labels, Ld, (size_t)T * n * 4, cudaMemcpyDeviceToHost, s));
   }
   CCM_CUDA(cudaStreamSynchronize(s));
   c->last_profile.kernel_launches = c->launches - launches0;

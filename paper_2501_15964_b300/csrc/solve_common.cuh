@@ -27,6 +27,11 @@ struct SolveArgs {
   // through eperm (new -> old edge, ~id = endpoints swapped: the row's sign flips)
   const int* perm = nullptr;
   const int* eperm = nullptr;
+  // host destination of X (caller's host memory; Xout is then a device staging
+  // buffer): each gamma's rows are copied on copy_stream while the next solves
+  double* Xhost = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_event = nullptr;
 
   // Algorithmic bytes of one Newton-CG operator launch (each datum once):
   // R read and W written (n x ld each), Minv (n), the yhat rows of the m_out

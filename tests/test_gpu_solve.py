@@ -318,3 +318,37 @@ def test_relabelled_solve_matches_plain_order(ccm, precision):
     assert stb[0]["status"] == 0
     Xb = Xb.cpu().numpy()
     assert np.linalg.norm(Xb[0] - runs[0][0][2]) <= TOL * np.linalg.norm(runs[0][0][2])
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_host_outputs_equal_device_outputs(ccm, engine):
+    """X and labels written to pinned (and pageable) host memory by the library
+    (each gamma's X copied while the next one solves) equal the device outputs
+    bit for bit; U must stay device memory."""
+    rng = np.random.default_rng(31)
+    n, d = (3000, 5) if engine == 1 else (300, 5)
+    cent = rng.normal(0, 4, size=(6, d))
+    A = cent[rng.integers(0, 6, n)] + 0.7 * rng.normal(size=(n, d))
+    At = torch.tensor(A, device="cuda:0")
+    Et, wt, _ = ccm.build_graph(At, 8, 0.0)
+    g = [0.01, 0.1, 0.5, 2.0]
+    X0, L0, _, st0 = ccm.solve_path(At, Et, wt, g, tol=SOLVE_TOL, engine=engine)
+    for pinned in (True, False):
+        Xh = torch.empty((len(g), n, d), dtype=torch.float64)
+        Lh = torch.empty((len(g), n), dtype=torch.int32)
+        if pinned:
+            Xh, Lh = Xh.pin_memory(), Lh.pin_memory()
+        X1, L1, _, st1 = ccm.solve_path(At, Et, wt, g, tol=SOLVE_TOL, engine=engine,
+                                        X_out=Xh, labels_host=Lh)
+        assert X1.data_ptr() == Xh.data_ptr() and L1.data_ptr() == Lh.data_ptr()
+        assert torch.equal(Xh, X0.cpu()) and torch.equal(Lh, L0.cpu()), pinned
+        assert [s["n_clusters"] for s in st1] == [s["n_clusters"] for s in st0]
+    E = torch.empty((len(g), Et.shape[0], d), dtype=torch.float64)
+    lib = ccm._lib.load_library()
+    ctx = ccm.api.default_context(0)
+    garr = (ccm._lib.C.c_double * len(g))(*g)
+    opt = ccm.api.make_options(engine=engine)
+    st = lib.ccm_solve_path(ctx.handle, At.data_ptr(), n, d, Et.data_ptr(), wt.data_ptr(),
+                            Et.shape[0], garr, len(g), 2, SOLVE_TOL, ccm._lib.C.byref(opt),
+                            X0.data_ptr(), None, E.data_ptr(), None, None)
+    assert st == 1  # CCM_ERR_INVALID_ARG: U in host memory
