@@ -435,8 +435,9 @@ struct GridEngine {
     {
       const DebugBounds hb{(long long)n, (long long)m, 0, 0, 0};
       CCM_CUDA(cudaMemcpyToSymbolAsync(g_bounds, &hb, sizeof(hb), 0, cudaMemcpyHostToDevice, s));
-      // fault injection for the tests of this build: one incidence record gets an
-      // out-of-range endpoint, which the checks must catch before any access
+      // fault injection for the tests of the bounds-checked library: one incidence
+      // record gets an out-of-range endpoint, which the checks must catch before any
+      // access
       if (getenv("CCM_DEBUG_CORRUPT") && m > 0) {
         const int bad = (int)n + 3;
         CCM_CUDA(cudaMemcpyAsync(&inc[0].y, &bad, sizeof(int), cudaMemcpyHostToDevice, s));
