@@ -908,9 +908,15 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
     a.perm = r.perm;
     a.eperm = r.eperm;
   }
+  // no copy into the caller's host memory may outlive the call: the copy stream
+  // is drained on every way out (the labels below overlap the last gamma's copy)
+  struct CopyDrain {
+    cudaStream_t cs;
+    ~CopyDrain() {
+      if (cs) cudaStreamSynchronize(cs);
+    }
+  } drain{x_host ? c->copy_stream : nullptr};
   int st = solve_grid(c, a, s);
-  // no copy into the caller's host memory may outlive the call
-  if (x_host) CCM_CUDA(cudaStreamSynchronize(c->copy_stream));
   if (st != CCM_OK && st != CCM_ERR_NOT_CONVERGED) return st;
   if (labels) {
     for (int t = 0; t < T; ++t) {
@@ -923,6 +929,7 @@ extern "C" int ccm_solve_path(ccm_ctx* x, const double* A, int64_t n, int32_t d,
       CCM_CUDA(cudaMemcpyAsync(labels, Ld, (size_t)T * n * 4, cudaMemcpyDeviceToHost, s));
   }
   CCM_CUDA(cudaStreamSynchronize(s));
+  if (x_host) CCM_CUDA(cudaStreamSynchronize(c->copy_stream));
   c->last_profile.kernel_launches = c->launches - launches0;
   if (st == CCM_ERR_NOT_CONVERGED) set_error("ccm_solve_path: some gamma hit an iteration cap");
   return st;
